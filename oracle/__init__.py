@@ -1,0 +1,47 @@
+"""Oracle for the FFT stencil path: plain, slow, obviously correct, CPU, FP64.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import or call anything in
+this package. The product path (``paper_2105_06676_gb300``) never imports it,
+and this package imports nothing from the product path: the two share no
+kernels, headers, helpers, tables or constants. The only thing both sides
+consume is the seeded input generator module, which holds none of the method's
+arithmetic.
+
+Contents
+--------
+``stencil_loop``         the plain definition a_{t+1} = S a_t written out as a
+                         double-buffered nested loop in C (periodic and
+                         zero-Dirichlet), compiled with gcc. Paper Sec. 1
+                         "Problem Specification" and the looping codes of
+                         Fig. "looping-code".
+``spectral``             the paper's StencilFFT-P steps in numpy FP64 (first
+                         column of S, Multi-FFT, repeated squaring, pointwise
+                         product, inverse Multi-FFT), Sec. 4 and
+                         Fig. "stencil-fft-algorithm-dD"; closed-form symbol,
+                         Appendix "Proof of Eigenvalue-FFT Relation".
+``recursive_boundary``   StencilFFT-A and RecursiveBoundary in numpy FP64,
+                         Sec. 5 and Fig. "stencil-fft-algorithm-1D-aperiodic".
+
+Every function is pinned by ``tests/test_oracle_pins.py`` against values the
+paper prints, closed forms, invariants and brute force.
+"""
+from .stencil_loop import (  # noqa: F401
+    build_oracle_library,
+    oracle_library_path,
+    oracle_threads,
+    stencil_loop,
+)
+from .spectral import (  # noqa: F401
+    dft_naive,
+    first_column,
+    stencil_fft_periodic,
+    symbol_closed_form,
+    symbol_multi_fft,
+    symbol_power,
+)
+from .recursive_boundary import (  # noqa: F401
+    boundary_distance,
+    recursive_boundary,
+    stencil_fft_aperiodic,
+)
