@@ -1,0 +1,306 @@
+"""Benchmark: effective N*T point-updates/s of the periodic FFT stencil solve.
+
+Workload: 2-D periodic 5-point stencil (centre 0.6, neighbours 0.1) on a
+4096 x 4096 grid, T = 10000, FP32 FFT passes with the FP64 symbol power
+(the headline), plus the same solve on the FP64 path. One step = one full
+solve (R2C pass, fused column pass with the on-the-fly FP64 Lambda^T multiply,
+C2R pass) of the seeded uniform[0, 1) grid; the grid is restored from a
+pristine copy and L2 is flushed (a 512 MiB write) between timed steps, outside
+the timed events.
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle (the
+FP64 nested loop on the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "effective N*T point-updates/s (2-D periodic 5-point StencilFFT-P)"
+UNIT = "point-updates/s"
+WORKLOAD = "star5_2d_periodic_4096x4096_T10000"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_sample(w, dims, T_sample, seed):
+    """Time the FP64 nested-loop oracle on T_sample steps of the full grid."""
+    import oracle
+    from paper_2105_06676_gb300 import workloads as wl
+    a0 = wl.grid_uniform(dims, seed)
+    oracle.build_oracle_library()
+    threads = oracle.oracle_threads()
+    t0 = time.perf_counter()
+    oracle.stencil_loop(a0, w, T_sample)
+    dt = time.perf_counter() - t0
+    n = math.prod(dims)
+    return n * T_sample / dt, threads, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2105_06676_gb300 import workloads as wl
+    wk = wl.star2d_4096("fp32")
+    T_sample = args.ref_steps_per_sample
+    vals = []
+    threads = 1
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wk.weights, wk.dims, max(1, T_sample // 4), wk.grid_seed)
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, threads, dt = cpu_oracle_sample(wk.weights, wk.dims, T_sample, wk.grid_seed)
+        vals.append(v)
+        t_all += dt
+    value = statistics.mean(vals)
+    sample = (f"{wk.dims[0]}x{wk.dims[1]} grid, {T_sample} of the {wk.T} steps per timed step "
+              "(the loop's work is linear in T)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": 1,
+                                        "grid": list(wk.dims), "T": wk.T},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_solve(plan, grid, pristine, flush, K, W, T):
+    """Per-step CUDA-event timing on the current stream; restore + flush outside."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        grid.copy_(pristine)
+        plan.run(grid, T)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for i in range(K):
+        grid.copy_(pristine)
+        flush.fill_(i)
+        starts[i].record(stream)
+        plan.run(grid, T)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-steps-per-sample", type=int, default=100)
+    ap.add_argument("--cpu-sample-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2105_06676_gb300 import StencilPlan
+    from paper_2105_06676_gb300 import workloads as wl
+
+    wk = wl.star2d_4096("fp32")
+    dims, T = wk.dims, wk.T
+    N = math.prod(dims)
+    a0 = wk.grid()
+
+    # replicas only: each rank solves its own copy of the workload
+    plan32 = StencilPlan(dims, wk.weights, "periodic", "fp32")
+    plan64 = StencilPlan(dims, wk.weights, "periodic", "fp64")
+    pristine32 = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    pristine64 = torch.tensor(a0, dtype=torch.float64, device="cuda")
+    g32 = pristine32.clone()
+    g64 = pristine64.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: FP32 path, per-kernel events on the launching stream
+    plan32.profile(True)
+    barrier()
+    with ClockSampler(local) as clk:
+        times32 = time_solve(plan32, g32, pristine32, flush, args.steps, args.warmup, T)
+    barrier()
+    prof = plan32.profile_read()          # includes warm-up launches; split below
+    plan32.profile(False)
+    ms32 = sum(times32) / len(times32)
+    if world > 1:
+        t = torch.tensor([ms32], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32 = float(t.item())
+    value = world * N * T / (ms32 * 1e-3)
+    assert plan32.status() == 0
+
+    # ---- FP64 path (secondary)
+    times64 = time_solve(plan64, g64, pristine64, flush, max(3, args.steps // 4), 3, T)
+    ms64 = sum(times64) / len(times64)
+
+    # ---- e2e through the C ABI with pinned host buffers (H2D + solve + D2H per step)
+    host_in = torch.tensor(a0, dtype=torch.float32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(2):
+        plan32.run_host(host_in, T, host_out)
+    barrier()
+    t0 = time.perf_counter()
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        plan32.run_host(host_in, T, host_out)
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_value = world * N * T / e2e_s
+
+    # ---- roofline of the dominant kernel (per-launch average over warm-up + timed launches)
+    peak, peak_kind = _peaks()
+    launches = {k: v[1] for k, v in prof.items()}
+    avg_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1]}
+    dominant = max(avg_ms, key=lambda k: avg_ms[k])
+    M = dims[1] // 2
+    half_bytes = dims[0] * (M + 1) * 8            # complex64 half spectrum
+    grid_bytes = N * 4
+    algo = {"rows_r2c": grid_bytes + half_bytes, "cols_fused": 2 * half_bytes,
+            "rows_c2r": half_bytes + grid_bytes}
+    achieved = algo[dominant] / (avg_ms[dominant] * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic_star5_2d_4096_fp32.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(dominant)
+        except Exception:
+            traffic = None
+    step_kernel_launches = sum(launches.values()) / (args.steps + args.warmup)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, threads, dt = cpu_oracle_sample(wk.weights, dims, args.cpu_sample_steps, wk.grid_seed)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 nested loop, full {dims[0]}x{dims[1]} grid, {args.cpu_sample_steps} "
+                         f"of the {T} steps ({dt:.1f} s; work is linear in T)"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FFT passes; FP64 symbol power)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(dims), "T": T, "global_batch": world,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed (512 MiB write) between timed steps; grid restored outside the events"},
+            "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": grid_bytes,
+                    "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3},
+            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind,
+                         "per_kernel_ms": {k: round(v, 5) for k, v in avg_ms.items()},
+                         "algorithmic_bytes": algo[dominant]},
+            "gpu_launches": int(round(step_kernel_launches * args.steps)),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * stencilfft.h -- C ABI of libstencilfft.so, a GB300 (sm_103a) solver that
+ * advances a linear, constant-coefficient stencil T time steps in
+ * O(N log N) work independent of T ("Fast Stencil Computations using Fast
+ * Fourier Transforms", arXiv 2105.06676).
+ *
+ * Problem (paper Sec. 1, "Problem Specification"; d-D form in the appendix
+ * "Supporting d-D Spatial Grids"): a grid a of shape l_1 x ... x l_d
+ * (d = 1..3, row-major, last axis contiguous) evolves by
+ *
+ *     a_{t+1}[i] = sum over m in [-r, r]^d of  w[m] * a_t[i + m]
+ *
+ * and the library returns a_T. Weights are given over the box [-r, r]^d in
+ * row-major order (entry (m_1 + r, ..., m_d + r)); in the paper's circulant
+ * notation (Sec. 4) the stored first column of S is s[(-m) mod l] = w[m].
+ *
+ *   STENCIL_PERIODIC        every index wraps (Sec. 1: the grid is a torus);
+ *                           solved by StencilFFT-P (Sec. 4, Eq. final_data:
+ *                           a_T = F^-1 Lambda^T F a_0).
+ *   STENCIL_ZERO_DIRICHLET  cells outside the grid read 0; solved by
+ *                           StencilFFT-A (Sec. 5): the interior from the
+ *                           periodic solve, the boundary's region of influence
+ *                           from RecursiveBoundary.
+ *
+ * Precision: STENCIL_FP64 grids are double and every step runs in FP64.
+ * STENCIL_FP32 grids are float; the FFT passes run in FP32 while the symbol
+ * Lambda and its T-th power are evaluated in FP64 on the GPU and rounded once.
+ *
+ * Supported sizes: every l_k a power of two with l_k >= 2r + 1 and l_k >= 4.
+ * Limits per precision are reported by stencil_max_axis().
+ *
+ * Errors: every call returns 0 (STENCIL_OK) or a negative STENCIL_E* code;
+ * stencil_strerror() names it. No call aborts the process. Device-side
+ * conditions (non-finite output) are latched in a per-plan status word read
+ * by stencil_status().
+ *
+ * Ownership: the caller owns every grid pointer. The library owns plans and
+ * all device workspace, allocated in stencil_plan (and, for zero-Dirichlet
+ * plans, on the first stencil_run for a given T) and released by
+ * stencil_destroy. A plan may be used from one host thread at a time.
+ */
+#ifndef STENCILFFT_H
+#define STENCILFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_plan_s* stencil_plan_t;
+
+enum stencil_boundary { STENCIL_PERIODIC = 0, STENCIL_ZERO_DIRICHLET = 1 };
+enum stencil_precision { STENCIL_FP64 = 0, STENCIL_FP32 = 1 };
+
+enum stencil_status_code {
+    STENCIL_OK = 0,
+    STENCIL_EINVAL = -1,       /* bad argument: null pointer, ndim, radius, T < 0, size */
+    STENCIL_ENOMEM = -2,       /* device or host allocation failed */
+    STENCIL_ECUDA = -3,        /* a CUDA runtime call failed */
+    STENCIL_ETIMEOUT = -4,     /* a bounded device wait gave up */
+    STENCIL_ENONFINITE = -5,   /* the solve produced Inf or NaN */
+    STENCIL_EQUEUEFULL = -6,   /* server queue has no free slot */
+    STENCIL_EUNSUPPORTED = -7  /* valid request outside this build's size limits */
+};
+
+/*
+ * Create a plan.
+ *   out       receives the plan handle (host pointer, non-null).
+ *   ndim      1, 2 or 3.
+ *   dims      host array of ndim axis lengths, row-major order.
+ *   radius    r >= 0 (paper's sigma for box stencils).
+ *   weights   host array of (2r+1)^ndim doubles (copied).
+ *   boundary  STENCIL_PERIODIC or STENCIL_ZERO_DIRICHLET.
+ *   precision STENCIL_FP64 or STENCIL_FP32.
+ * Allocates the FFT workspace and the twiddle and symbol tables on the
+ * current CUDA device and builds them there (twiddles by FP64 sincospi,
+ * paper Sec. 4 "Step 1").
+ */
+int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                 const double* weights, int boundary, int precision);
+
+/*
+ * Advance grid by T >= 0 steps in place (paper Fig. "stencil-fft-algorithm-dD"
+ * for periodic plans, Fig. "stencil-fft-algorithm-1D-aperiodic" for
+ * zero-Dirichlet plans).
+ *   grid    device pointer to prod(dims) elements (double for FP64 plans,
+ *           float for FP32 plans), 16-byte aligned.
+ *   stream  a cudaStream_t (NULL = legacy default stream).
+ * Enqueues work only; returns before the GPU finishes. T == 0 is a no-op.
+ */
+int stencil_run(stencil_plan_t plan, void* grid, int64_t T, void* stream);
+
+/*
+ * End-to-end variant of stencil_run on host memory: copies host_in to a
+ * plan-owned device grid, solves, copies the result to host_out and
+ * synchronises the stream. host_in and host_out hold prod(dims) elements of
+ * the plan's precision (pinned memory gives full copy bandwidth; they may
+ * alias).
+ */
+int stencil_run_host(stencil_plan_t plan, const void* host_in, void* host_out,
+                     int64_t T, void* stream);
+
+/*
+ * Symbol power (paper Sec. 4 "Step 2", repeated squaring of Lambda = F s):
+ * writes V[k] = Lambda[k]^T for the half spectrum k_d = 0 .. l_d/2 of the
+ * last axis and every k_1..k_{d-1}, as interleaved complex FP64 in row-major
+ * order of shape (l_1, ..., l_{d-1}, l_d/2 + 1), to the device buffer out.
+ * Lambda[k] = sum_m w[m] exp(+2 pi i sum_j m_j k_j / l_j) (appendix "Proof of
+ * Eigenvalue-FFT Relation" with the unnormalised forward DFT of Sec. 4).
+ * Same FP64 device arithmetic as the solver's fused spectral multiply, without
+ * the 1/N scale and without the underflow shortcut.
+ */
+int stencil_symbol_power(stencil_plan_t plan, int64_t T, void* out, void* stream);
+
+/*
+ * Synchronise stream and report the plan's latched device status:
+ * STENCIL_OK, STENCIL_ENONFINITE (Inf/NaN written by a solve since the last
+ * call) or STENCIL_ECUDA. Clears the latch.
+ */
+int stencil_status(stencil_plan_t plan, void* stream);
+
+/*
+ * Base-case cutoff of RecursiveBoundary for zero-Dirichlet plans (paper
+ * Fig. "stencil-fft-algorithm-1D-aperiodic", Base Case): subproblems with
+ * T < cutoff are advanced by the direct loop. cutoff >= 2, or 0 for the
+ * automatic choice. The result does not depend on it beyond rounding.
+ */
+int stencil_plan_set_cutoff(stencil_plan_t plan, int64_t cutoff);
+
+/*
+ * Per-kernel timing (measurement support, not part of the paper's method).
+ * While enabled, every kernel launch of stencil_run on this plan is bracketed
+ * by CUDA events recorded on the launching stream. stencil_profile_read
+ * waits for those events and returns, per kernel kind k < nkinds, the summed
+ * milliseconds ms[k] and the launch count launches[k] since the last read,
+ * then resets them. stencil_profile_kind_name gives the static name of kind k
+ * (NULL past the last kind).
+ */
+int stencil_profile_enable(stencil_plan_t plan, int enable);
+int stencil_profile_read(stencil_plan_t plan, double* ms, int64_t* launches, int nkinds);
+const char* stencil_profile_kind_name(int kind);
+
+/* Release a plan and all its device memory (synchronises the device). */
+int stencil_destroy(stencil_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* stencil_strerror(int code);
+
+/*
+ * Largest supported axis length for (ndim, precision, axis). axis 0..ndim-1.
+ * Returns 0 for invalid arguments.
+ */
+int64_t stencil_max_axis(int ndim, int precision, int axis);
+
+/* Bytes of device workspace a plan with these arguments allocates (0 on error). */
+size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int boundary,
+                               int precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCILFFT_H */

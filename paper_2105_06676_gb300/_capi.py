@@ -1,0 +1,77 @@
+"""ctypes declarations of the C ABI in include/stencilfft.h (argument marshalling only).
+
+Loading fails loudly when libstencilfft.so has not been built: there is no
+CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstencilfft.so")
+
+STENCIL_PERIODIC = 0
+STENCIL_ZERO_DIRICHLET = 1
+STENCIL_FP64 = 0
+STENCIL_FP32 = 1
+
+STATUS = {
+    0: "STENCIL_OK", -1: "STENCIL_EINVAL", -2: "STENCIL_ENOMEM", -3: "STENCIL_ECUDA",
+    -4: "STENCIL_ETIMEOUT", -5: "STENCIL_ENONFINITE", -6: "STENCIL_EQUEUEFULL",
+    -7: "STENCIL_EUNSUPPORTED",
+}
+
+# (name, restype, argtypes) for every entry point the header declares.
+_c = ctypes
+_vp = _c.c_void_p
+_i64p = _c.POINTER(_c.c_int64)
+_dp = _c.POINTER(_c.c_double)
+SIGNATURES = [
+    ("stencil_plan", _c.c_int, [_c.POINTER(_vp), _c.c_int, _i64p, _c.c_int, _dp, _c.c_int, _c.c_int]),
+    ("stencil_run", _c.c_int, [_vp, _vp, _c.c_int64, _vp]),
+    ("stencil_run_host", _c.c_int, [_vp, _vp, _vp, _c.c_int64, _vp]),
+    ("stencil_symbol_power", _c.c_int, [_vp, _c.c_int64, _vp, _vp]),
+    ("stencil_status", _c.c_int, [_vp, _vp]),
+    ("stencil_destroy", _c.c_int, [_vp]),
+    ("stencil_strerror", _c.c_char_p, [_c.c_int]),
+    ("stencil_max_axis", _c.c_int64, [_c.c_int, _c.c_int, _c.c_int]),
+    ("stencil_workspace_bytes", _c.c_size_t, [_c.c_int, _i64p, _c.c_int, _c.c_int, _c.c_int]),
+    ("stencil_plan_set_cutoff", _c.c_int, [_vp, _c.c_int64]),
+    ("stencil_profile_enable", _c.c_int, [_vp, _c.c_int]),
+    ("stencil_profile_read", _c.c_int, [_vp, _c.POINTER(_c.c_double), _i64p, _c.c_int]),
+    ("stencil_profile_kind_name", _c.c_char_p, [_c.c_int]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().stencil_strerror(code).decode() if _lib is not None else STATUS.get(code, "?")
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({msg})")
+
+
+def lib():
+    """The loaded library; raises if it was never built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def check(code: int, where: str) -> None:
+    if code != 0:
+        raise StencilError(code, where)

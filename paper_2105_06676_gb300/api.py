@@ -1,0 +1,150 @@
+"""Thin Python binding over libstencilfft.so (argument marshalling only).
+
+Every step of a solve runs in the library's CUDA kernels. PyTorch is used for
+device memory and streams: a grid is a CUDA tensor, the stream is
+``torch.cuda.current_stream()`` unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+
+_BOUNDARY = {"periodic": _capi.STENCIL_PERIODIC, "dirichlet": _capi.STENCIL_ZERO_DIRICHLET,
+             "zero_dirichlet": _capi.STENCIL_ZERO_DIRICHLET}
+_PRECISION = {"fp64": _capi.STENCIL_FP64, "fp32": _capi.STENCIL_FP32}
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def max_axis(ndim: int, precision: str, axis: int) -> int:
+    return int(_capi.lib().stencil_max_axis(ndim, _PRECISION[precision], axis))
+
+
+def workspace_bytes(dims, radius: int, boundary: str, precision: str) -> int:
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    return int(_capi.lib().stencil_workspace_bytes(len(dims), d, int(radius),
+                                                  _BOUNDARY[boundary], _PRECISION[precision]))
+
+
+class StencilPlan:
+    """A plan for advancing grids of one shape by one stencil (stencil_plan)."""
+
+    def __init__(self, dims, weights, boundary: str = "periodic", precision: str = "fp32"):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        dims = tuple(int(x) for x in dims)
+        if w.ndim != len(dims) or len(set(w.shape)) != 1 or w.shape[0] % 2 != 1:
+            raise ValueError("weights must have shape (2r+1,)*ndim")
+        self.dims = dims
+        self.radius = (w.shape[0] - 1) // 2
+        self.boundary = boundary
+        self.precision = precision
+        self.weights = w
+        self._handle = ctypes.c_void_p()
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        rc = _capi.lib().stencil_plan(ctypes.byref(self._handle), len(dims), d, self.radius,
+                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      _BOUNDARY[boundary], _PRECISION[precision])
+        _capi.check(rc, "stencil_plan")
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def set_cutoff(self, cutoff: int) -> None:
+        _capi.check(_capi.lib().stencil_plan_set_cutoff(self._handle, int(cutoff)),
+                    "stencil_plan_set_cutoff")
+
+    def run(self, grid, T: int, stream=None):
+        """Advance a CUDA tensor of shape dims in place by T steps (async); returns it."""
+        if not grid.is_cuda or grid.dtype != self.dtype or tuple(grid.shape) != self.dims \
+                or not grid.is_contiguous():
+            raise ValueError(f"grid must be a contiguous CUDA {self.dtype} tensor of shape {self.dims}")
+        rc = _capi.lib().stencil_run(self._handle, ctypes.c_void_p(grid.data_ptr()), int(T),
+                                     _stream_ptr(stream))
+        _capi.check(rc, "stencil_run")
+        return grid
+
+    def run_host(self, host_in, T: int, host_out=None, stream=None):
+        """End-to-end solve of a host (CPU) tensor: H2D copy, solve, D2H copy, sync."""
+        import torch
+        if host_in.is_cuda or host_in.dtype != self.dtype or tuple(host_in.shape) != self.dims:
+            raise ValueError("host_in must be a CPU tensor of the plan's shape and dtype")
+        host_in = host_in.contiguous()
+        if host_out is None:
+            host_out = torch.empty_like(host_in)
+        rc = _capi.lib().stencil_run_host(self._handle, ctypes.c_void_p(host_in.data_ptr()),
+                                          ctypes.c_void_p(host_out.data_ptr()), int(T),
+                                          _stream_ptr(stream))
+        _capi.check(rc, "stencil_run_host")
+        return host_out
+
+    def symbol_power(self, T: int, stream=None):
+        """Lambda^T on the half spectrum, complex128 CUDA tensor (stencil_symbol_power)."""
+        import torch
+        shape = self.dims[:-1] + (self.dims[-1] // 2 + 1,)
+        out = torch.empty(shape + (2,), dtype=torch.float64, device="cuda")
+        rc = _capi.lib().stencil_symbol_power(self._handle, int(T), ctypes.c_void_p(out.data_ptr()),
+                                              _stream_ptr(stream))
+        _capi.check(rc, "stencil_symbol_power")
+        return torch.view_as_complex(out)
+
+    def profile(self, enable: bool = True) -> None:
+        """Bracket every kernel launch of later runs with CUDA events (stencil_profile_enable)."""
+        _capi.check(_capi.lib().stencil_profile_enable(self._handle, int(bool(enable))),
+                    "stencil_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total ms, launches)} since the last read (synchronises)."""
+        nk = 32
+        ms = (ctypes.c_double * nk)()
+        cnt = (ctypes.c_int64 * nk)()
+        _capi.check(_capi.lib().stencil_profile_read(self._handle, ms, cnt, nk), "stencil_profile_read")
+        out = {}
+        for k in range(nk):
+            name = _capi.lib().stencil_profile_kind_name(k)
+            if name is None:
+                break
+            if cnt[k]:
+                out[name.decode()] = (float(ms[k]), int(cnt[k]))
+        return out
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return the latched status code (0 or a negative code)."""
+        return int(_capi.lib().stencil_status(self._handle, _stream_ptr(stream)))
+
+    def close(self):
+        if self._handle:
+            _capi.lib().stencil_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(grid, weights, T: int, boundary: str = "periodic", stream=None):
+    """One-shot solve of a CUDA tensor in place (builds and frees a plan)."""
+    precision = "fp32" if str(grid.dtype) == "torch.float32" else "fp64"
+    plan = StencilPlan(tuple(grid.shape), weights, boundary, precision)
+    try:
+        plan.run(grid, T, stream)
+        import torch
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    finally:
+        plan.close()
+    return grid

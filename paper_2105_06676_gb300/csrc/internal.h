@@ -1,0 +1,62 @@
+// Internal interfaces between the host plan code and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "symbol.cuh"
+
+namespace sfft {
+
+// Elements per thread held in registers by the shared-memory FFT.
+constexpr int kEPT = 16;
+// Threads per CTA upper bounds (launch bounds of the FFT kernels).
+constexpr int kMaxThreadsF32 = 1024;
+constexpr int kMaxThreadsF64 = 512;
+// Largest per-CTA dynamic shared memory the FFT kernels request.
+constexpr int kSmemBudget = 200 * 1024;
+
+// A batch of strided columns: the FFT runs along an axis of length n = 2^log2n
+// with element stride S; the batch is (outer, mid, inner) with
+// address = base + o*os + m*ms + j*S + i for i < inner_valid, and `cols`
+// consecutive inner indices per CTA.
+struct ColGeom {
+    int log2n;
+    long long S;
+    int outer;
+    long long os;
+    int mid;
+    long long ms;
+    int inner_valid;
+    int cols_log2;
+};
+
+// Launchers (templated on the real type; instantiated for float and double).
+template <typename R>
+cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
+                            const SymbolParams& p, int* status, cudaStream_t s);
+template <typename R>
+cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, int nrows,
+                            const void* tw, int twn_log2, cudaStream_t s);
+template <typename R>
+cudaError_t launch_rows_c2r(const void* H, R* grid, long long Mp, int n_log2, int nrows,
+                            const void* tw, int twn_log2, int* status, cudaStream_t s);
+template <typename R>
+cudaError_t launch_cols(void* H, const ColGeom& g, int dir, const void* tw, int twn_log2,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                              const SymbolParams& p, cudaStream_t s);
+template <typename R>
+cudaError_t launch_twiddles(void* tw, int twn_log2, cudaStream_t s);
+cudaError_t launch_axis_table(double2* E64, float2* E32, int len, cudaStream_t s);
+cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_half,
+                                long long total, cudaStream_t s);
+
+// Number of columns per CTA the column kernels use for a transform of 2^log2n.
+int cols_log2_for(int log2n, int elem_bytes, int max_threads);
+// Rows per CTA of the row kernels.
+int rows_per_cta_for(int n_log2, int elem_bytes, int max_threads);
+
+}  // namespace sfft

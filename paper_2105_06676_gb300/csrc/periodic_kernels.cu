@@ -1,0 +1,453 @@
+// StencilFFT-P kernels (paper Sec. 4, Fig. "stencil-fft-algorithm-dD").
+//
+// A real grid of shape l_1 x ... x l_d is solved in place by
+//   * rows_r2c   : FFT along the contiguous last axis. A real row of L = 2n
+//                  values is read as n complex pairs, transformed, and split
+//                  into the half spectrum X[0..n] (Hermitian symmetry of a real
+//                  input), written to the workspace H (row stride Mp).
+//   * cols       : FFT along a strided axis of H (forward or inverse).
+//   * cols_fused : forward FFT along axis 0, multiply by V[k] = Lambda[k]^T / N
+//                  (Steps 2 and 3: repeated squaring and the pointwise
+//                  product), inverse FFT along axis 0, all in shared memory:
+//                  one read and one write of H.
+//   * rows_c2r   : inverse of rows_r2c (Step 4), writes the real grid.
+//   * fused_1d   : for d = 1 the whole solve (R2C, multiply, C2R) in one CTA
+//                  per row.
+// The spectrum never needs reordering: every pass returns natural order, so
+// V is evaluated at the natural frequency of each element.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace sfft {
+
+template <typename R> struct MaxT;
+template <> struct MaxT<float> { static constexpr int v = kMaxThreadsF32; };
+template <> struct MaxT<double> { static constexpr int v = kMaxThreadsF64; };
+
+__device__ __forceinline__ bool finite2(float2 v) { return isfinite(v.x) && isfinite(v.y); }
+__device__ __forceinline__ bool finite2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
+
+// ---------------------------------------------------------------------------
+// fused 1-D solve: rows of L = 2n reals, one CTA holds `rpc` rows
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(MaxT<R>::v)
+k_fused_1d(R* __restrict__ grid, int n_log2, int nrows, int rpc,
+           const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
+           const __grid_constant__ SymbolParams p, int* status) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2;
+    const int ss = seq_stride(n);
+    const int row0 = blockIdx.x * rpc;
+    const int rows = min(rpc, nrows - row0);
+    C* rowp = reinterpret_cast<C*>(grid) + (size_t)row0 * n;  // row c, pair j at rowp[c*n + j]
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int c = e >> n_log2, j = e & (n - 1);
+        sm[c * ss + spad(j)] = rowp[e];
+    }
+    __syncthreads();
+    fft_smem<-1, kEPT>(sm, n_log2, rows, tw, twn_log2);
+    const int half = n / 2 + 1;
+    const int sh = twn_log2 - n_log2 - 1;  // W^k = exp(-2 pi i k / 2n) = tw[k << sh]
+    for (int e = threadIdx.x; e < rows * half; e += blockDim.x) {
+        const int c = e / half, k = e - c * half;
+        C* s = sm + c * ss;
+        const int ik = spad(k & (n - 1)), ink = spad((n - k) & (n - 1));
+        const C zk = s[ik], znk = s[ink];
+        const C xe = cscale(cadd(zk, cconj(znk)), (R)0.5);
+        const C xo = cscale(cmul_mi(csub(zk, cconj(znk))), (R)0.5);
+        const C wk = tw[k << sh];
+        const C t = cmul(wk, xo);
+        const C Xk = cadd(xe, t);
+        const C Xnk = cconj(csub(xe, t));
+        int kk = k;
+        const C Vk = spectral_multiplier<C>(p, &kk);
+        kk = n - k;
+        const C Vnk = spectral_multiplier<C>(p, &kk);
+        const C Yk = cmul(Vk, Xk), Ynk = cmul(Vnk, Xnk);
+        // inverse pre-processing: Z'[q] = (Y[q] + conj Y[n-q]) + i conj(W^q) (Y[q] - conj Y[n-q])
+        const C zpk = cadd(cadd(Yk, cconj(Ynk)), cmul_i(cmul(cconj(wk), csub(Yk, cconj(Ynk)))));
+        // conj(W^(n-k)) = -W^k
+        const C zpnk = csub(cadd(Ynk, cconj(Yk)), cmul_i(cmul(wk, csub(Ynk, cconj(Yk)))));
+        s[ik] = zpk;
+        if (k != 0 && 2 * k != n) s[ink] = zpnk;
+    }
+    __syncthreads();
+    fft_smem<+1, kEPT>(sm, n_log2, rows, tw, twn_log2);
+    bool bad = false;
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int c = e >> n_log2, j = e & (n - 1);
+        const C v = sm[c * ss + spad(j)];
+        bad |= !finite2(v);
+        rowp[e] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// real rows -> half spectrum rows (n + 1 complex values, row stride Mp)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(MaxT<R>::v)
+k_rows_r2c(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, long long Mp,
+           int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
+           int twn_log2) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2;
+    const int ss = seq_stride(n);
+    const long long row0 = (long long)blockIdx.x * rpc;
+    const int rows = (int)min((long long)rpc, nrows - row0);
+    const C* rowp = reinterpret_cast<const C*>(grid) + row0 * n;
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int c = e >> n_log2, j = e & (n - 1);
+        sm[c * ss + spad(j)] = __ldg(rowp + e);
+    }
+    __syncthreads();
+    fft_smem<-1, kEPT>(sm, n_log2, rows, tw, twn_log2);
+    const int sh = twn_log2 - n_log2 - 1;
+    const int np1 = n + 1;
+    for (int e = threadIdx.x; e < rows * np1; e += blockDim.x) {
+        const int c = e / np1, k = e - c * np1;
+        const C* s = sm + c * ss;
+        const C zk = s[spad(k & (n - 1))], znk = s[spad((n - k) & (n - 1))];
+        const C xe = cscale(cadd(zk, cconj(znk)), (R)0.5);
+        const C xo = cscale(cmul_mi(csub(zk, cconj(znk))), (R)0.5);
+        const C wk = tw[k << sh];
+        H[(row0 + c) * Mp + k] = cadd(xe, cmul(wk, xo));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// half spectrum rows -> real rows
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(MaxT<R>::v)
+k_rows_c2r(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, long long Mp,
+           int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
+           int twn_log2, int* status) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2;
+    const int ss = seq_stride(n);
+    const long long row0 = (long long)blockIdx.x * rpc;
+    const int rows = (int)min((long long)rpc, nrows - row0);
+    const int sh = twn_log2 - n_log2 - 1;
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int c = e >> n_log2, k = e & (n - 1);
+        const C* h = H + (row0 + c) * Mp;
+        const C yk = __ldg(h + k), ynk = __ldg(h + (n - k));
+        const C wk = tw[k << sh];
+        sm[c * ss + spad(k)] =
+            cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
+    }
+    __syncthreads();
+    fft_smem<+1, kEPT>(sm, n_log2, rows, tw, twn_log2);
+    C* rowp = reinterpret_cast<C*>(grid) + row0 * n;
+    bool bad = false;
+    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+        const int c = e >> n_log2, j = e & (n - 1);
+        const C v = sm[c * ss + spad(j)];
+        bad |= !finite2(v);
+        rowp[e] = v;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// strided column FFTs (forward or inverse), and the fused
+// forward * V * inverse pass along axis 0
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ void load_cols(C* sm, const C* __restrict__ base, const ColGeom& g,
+                                          int i0) {
+    const int n = 1 << g.log2n;
+    const int cols = 1 << g.cols_log2;
+    const int ss = seq_stride(n);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int j = e >> g.cols_log2, c = e & (cols - 1);
+        C v{0, 0};
+        if (i0 + c < g.inner_valid) v = base[(long long)j * g.S + c];
+        sm[c * ss + spad(j)] = v;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void store_cols(const C* sm, C* __restrict__ base, const ColGeom& g,
+                                           int i0) {
+    const int n = 1 << g.log2n;
+    const int cols = 1 << g.cols_log2;
+    const int ss = seq_stride(n);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int j = e >> g.cols_log2, c = e & (cols - 1);
+        if (i0 + c < g.inner_valid) base[(long long)j * g.S + c] = sm[c * ss + spad(j)];
+    }
+}
+
+template <typename R, int DIR>
+__global__ void __launch_bounds__(MaxT<R>::v)
+k_cols(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
+       const typename CxOf<R>::T* __restrict__ tw, int twn_log2) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int i0 = blockIdx.x << g.cols_log2;
+    C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0;
+    load_cols(sm, base, g, i0);
+    __syncthreads();
+    const int cols = min(1 << g.cols_log2, g.inner_valid - i0);
+    fft_smem<DIR, kEPT>(sm, g.log2n, cols, tw, twn_log2);
+    store_cols(sm, base, g, i0);
+}
+
+// Fused pass along axis 0 of the half spectrum. Frequencies: k_0 is the FFT
+// index; for d = 2 the inner index is k_1; for d = 3 the mid index is k_1 and
+// the inner index k_2.
+template <typename R>
+__global__ void __launch_bounds__(MaxT<R>::v)
+k_cols_fused(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
+             const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
+             const __grid_constant__ SymbolParams p) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int i0 = blockIdx.x << g.cols_log2;
+    C* base = H + (long long)blockIdx.y * g.ms + i0;
+    load_cols(sm, base, g, i0);
+    __syncthreads();
+    const int cols = min(1 << g.cols_log2, g.inner_valid - i0);
+    fft_smem<-1, kEPT>(sm, g.log2n, cols, tw, twn_log2);
+    const int n = 1 << g.log2n;
+    const int ss = seq_stride(n);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int c = e >> g.log2n, j = e & (n - 1);
+        int k[3];
+        k[0] = j;
+        if (p.ndim == 2) {
+            k[1] = i0 + c;
+        } else {
+            k[1] = blockIdx.y;
+            k[2] = i0 + c;
+        }
+        const C v = spectral_multiplier<C>(p, k);
+        C* q = sm + c * ss + spad(j);
+        *q = cmul(*q, v);
+    }
+    __syncthreads();
+    fft_smem<+1, kEPT>(sm, g.log2n, cols, tw, twn_log2);
+    store_cols(sm, base, g, i0);
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_twiddles(typename CxOf<R>::T* tw, int twn_log2) {
+    const int n = 1 << twn_log2;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)n, &s, &c);   // exp(-2 pi i m / n)
+        tw[m] = typename CxOf<R>::T{(R)c, (R)s};
+    }
+}
+
+__global__ void k_axis_table(double2* E64, float2* E32, int len) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < len; q += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)q / (double)len, &s, &c);  // exp(+2 pi i q / len)
+        E64[q] = double2{c, s};
+        E32[q] = float2{(float)c, (float)s};
+    }
+}
+
+// V[k] = Lambda[k]^T (FP64, natural order of the half spectrum).
+__global__ void k_symbol_table(double2* out, const __grid_constant__ SymbolParams p,
+                               int nlast_half, long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int k[3];
+        long long rest = e;
+        k[p.ndim - 1] = (int)(rest % nlast_half);
+        rest /= nlast_half;
+        for (int a = p.ndim - 2; a >= 0; --a) {
+            k[a] = (int)(rest % p.len[a]);
+            rest /= p.len[a];
+        }
+        out[e] = lambda_pow64(p, k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+int cols_log2_for(int log2n, int elem_bytes, int max_threads) {
+    const int n = 1 << log2n;
+    int cl = 0;
+    while (cl < 4) {
+        const int next = 1 << (cl + 1);
+        const long long smem = (long long)next * seq_stride(n) * elem_bytes;
+        if (smem > kSmemBudget || (long long)next * n > (long long)kEPT * max_threads) break;
+        ++cl;
+    }
+    return cl;
+}
+
+int rows_per_cta_for(int n_log2, int elem_bytes, int max_threads) {
+    const int n = 1 << n_log2;
+    int rpc = 1;
+    while (rpc * 2 * n <= 4096 && (long long)rpc * 2 * seq_stride(n) * elem_bytes <= kSmemBudget &&
+           rpc * 2 * n <= kEPT * max_threads)
+        rpc *= 2;
+    return rpc;
+}
+
+static int threads_for(long long elems, int max_threads) {
+    long long t = (elems + kEPT - 1) / kEPT;
+    t = (t + 31) / 32 * 32;
+    if (t < 32) t = 32;
+    if (t > max_threads) t = max_threads;
+    return (int)t;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
+                            const SymbolParams& p, int* status, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
+    cudaError_t err = set_smem(k_fused_1d<R>, smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (nrows + rpc - 1) / rpc;
+    k_fused_1d<R><<<blocks, threads, smem, s>>>(grid, n_log2, nrows, rpc,
+                                                 static_cast<const C*>(tw), twn_log2, p, status);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, int nrows,
+                            const void* tw, int twn_log2, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
+    cudaError_t err = set_smem(k_rows_r2c<R>, smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (nrows + rpc - 1) / rpc;
+    k_rows_r2c<R><<<blocks, threads, smem, s>>>(grid, static_cast<C*>(H), Mp, n_log2, nrows, rpc,
+                                                 static_cast<const C*>(tw), twn_log2);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_rows_c2r(const void* H, R* grid, long long Mp, int n_log2, int nrows,
+                            const void* tw, int twn_log2, int* status, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
+    cudaError_t err = set_smem(k_rows_c2r<R>, smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (nrows + rpc - 1) / rpc;
+    k_rows_c2r<R><<<blocks, threads, smem, s>>>(static_cast<const C*>(H), grid, Mp, n_log2, nrows,
+                                                 rpc, static_cast<const C*>(tw), twn_log2, status);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cols(void* H, const ColGeom& g, int dir, const void* tw, int twn_log2,
+                        cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << g.log2n;
+    const int cols = 1 << g.cols_log2;
+    const size_t smem = (size_t)cols * seq_stride(n) * sizeof(C);
+    const int threads = threads_for((long long)cols * n, MaxT<R>::v);
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
+    cudaError_t err;
+    if (dir < 0) {
+        err = set_smem(k_cols<R, -1>, smem);
+        if (err != cudaSuccess) return err;
+        k_cols<R, -1><<<grid, threads, smem, s>>>(static_cast<C*>(H), g, static_cast<const C*>(tw),
+                                                   twn_log2);
+    } else {
+        err = set_smem(k_cols<R, +1>, smem);
+        if (err != cudaSuccess) return err;
+        k_cols<R, +1><<<grid, threads, smem, s>>>(static_cast<C*>(H), g, static_cast<const C*>(tw),
+                                                   twn_log2);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                              const SymbolParams& p, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << g.log2n;
+    const int cols = 1 << g.cols_log2;
+    const size_t smem = (size_t)cols * seq_stride(n) * sizeof(C);
+    const int threads = threads_for((long long)cols * n, MaxT<R>::v);
+    cudaError_t err = set_smem(k_cols_fused<R>, smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, 1);
+    k_cols_fused<R><<<grid, threads, smem, s>>>(static_cast<C*>(H), g, static_cast<const C*>(tw),
+                                                 twn_log2, p);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_twiddles(void* tw, int twn_log2, cudaStream_t s) {
+    const int n = 1 << twn_log2;
+    const int threads = 256;
+    const int blocks = (n + threads - 1) / threads;
+    k_twiddles<R><<<blocks, threads, 0, s>>>(static_cast<typename CxOf<R>::T*>(tw), twn_log2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axis_table(double2* E64, float2* E32, int len, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (len + threads - 1) / threads;
+    k_axis_table<<<blocks, threads, 0, s>>>(E64, E32, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_half,
+                                long long total, cudaStream_t s) {
+    const int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    k_symbol_table<<<(int)blocks, threads, 0, s>>>(out, p, nlast_half, total);
+    return cudaGetLastError();
+}
+
+#define SFFT_INSTANTIATE(R)                                                                        \
+    template cudaError_t launch_fused_1d<R>(R*, int, int, const void*, int, const SymbolParams&,   \
+                                            int*, cudaStream_t);                                   \
+    template cudaError_t launch_rows_r2c<R>(const R*, void*, long long, int, int, const void*,     \
+                                            int, cudaStream_t);                                    \
+    template cudaError_t launch_rows_c2r<R>(const void*, R*, long long, int, int, const void*,     \
+                                            int, int*, cudaStream_t);                              \
+    template cudaError_t launch_cols<R>(void*, const ColGeom&, int, const void*, int,              \
+                                        cudaStream_t);                                             \
+    template cudaError_t launch_cols_fused<R>(void*, const ColGeom&, const void*, int,             \
+                                              const SymbolParams&, cudaStream_t);                  \
+    template cudaError_t launch_twiddles<R>(void*, int, cudaStream_t);
+
+SFFT_INSTANTIATE(float)
+SFFT_INSTANTIATE(double)
+
+}  // namespace sfft

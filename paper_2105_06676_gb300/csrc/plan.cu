@@ -1,0 +1,468 @@
+// Host side of libstencilfft.so: plans, workspace, and the C ABI declared in
+// include/stencilfft.h.
+//
+// A periodic run is StencilFFT-P (paper Sec. 4, Fig. "stencil-fft-algorithm-dD"):
+//   d = 1 : one fused kernel per row (R2C, multiply by V, C2R in shared memory);
+//   d = 2 : rows_r2c -> cols_fused(axis 0) -> rows_c2r;
+//   d = 3 : rows_r2c -> cols(axis 1, fwd) -> cols_fused(axis 0)
+//           -> cols(axis 1, inv) -> rows_c2r.
+// A zero-Dirichlet run is StencilFFT-A (Sec. 5), implemented in aperiodic.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/stencilfft.h"
+#include "internal.h"
+#include "plan_impl.h"
+
+using namespace sfft;
+
+// Profiler: events are pooled and only recorded while profiling is enabled.
+cudaEvent_t Profiler::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+void Profiler::begin(int kind, cudaStream_t s) {
+    if (!enabled) return;
+    Mark m{kind, get(), get()};
+    cudaEventRecord(m.a, s);
+    marks.push_back(m);
+}
+void Profiler::end(cudaStream_t s) {
+    if (!enabled || marks.empty()) return;
+    cudaEventRecord(marks.back().b, s);
+}
+cudaError_t Profiler::collect() {
+    cudaError_t first = cudaSuccess;
+    for (auto& m : marks) {
+        cudaError_t err = cudaEventSynchronize(m.b);
+        float t = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t, m.a, m.b);
+        if (err == cudaSuccess) {
+            ms[m.kind] += t;
+            launches[m.kind] += 1;
+        } else if (first == cudaSuccess) {
+            first = err;
+        }
+        pool.push_back(m.a);
+        pool.push_back(m.b);
+    }
+    marks.clear();
+    return first;
+}
+Profiler::~Profiler() {
+    for (auto& m : marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+namespace sfft {
+
+int ilog2_exact(int64_t v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+int64_t max_axis(int ndim, int precision, int axis) {
+    if (ndim < 1 || ndim > 3 || axis < 0 || axis >= ndim) return 0;
+    const bool f32 = precision == STENCIL_FP32;
+    if (axis == ndim - 1) return f32 ? 32768 : 16384;   // real rows: n = L/2 complex in one CTA
+    return f32 ? 16384 : 8192;                           // strided complex columns
+}
+
+static bool symmetric_weights(const double* w, int ndim, int r) {
+    const int W = 2 * r + 1;
+    int count = 1;
+    for (int a = 0; a < ndim; ++a) count *= W;
+    for (int i = 0; i < count; ++i) {
+        // index of -m: reverse every digit
+        int rest = i, mirror = 0, mul = 1;
+        for (int a = 0; a < ndim; ++a) {
+            const int digit = rest % W;
+            rest /= W;
+            mirror += (W - 1 - digit) * mul;
+            mul *= W;
+        }
+        if (w[i] != w[mirror]) return false;
+    }
+    return true;
+}
+
+// Symbol parameters for a periodic solve of a box of shape len[0..ndim-1]
+// with the plan's weights (optionally transposed weights for strips).
+SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
+                                const double2* const* E64, const float2* const* E32) {
+    SymbolParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.ndim = p->ndim;
+    sp.r = p->radius;
+    sp.T = (long long)T;
+    double N = 1.0;
+    for (int a = 0; a < p->ndim; ++a) {
+        sp.len[a] = (int)len[a];
+        N *= (double)len[a];
+        sp.E64[a] = E64[a];
+        sp.E32[a] = E32[a];
+    }
+    sp.scale = 1.0 / N;
+    sp.real_symbol = p->real_symbol ? 1 : 0;
+    double wsum = 0.0;
+    for (int i = 0; i < p->nweights; ++i) {
+        sp.w[i] = p->weights[i];
+        sp.w32[i] = (float)p->weights[i];
+        wsum += std::fabs(p->weights[i]);
+    }
+    // |Lambda - Lambda_fp32| <= sum|w| * 2^-16: a generous bound on the error of
+    // at most 343 products of <= 3 rounded table entries and a rounded weight.
+    sp.delta = (float)(wsum * std::ldexp(1.0, -16)) + 1e-30f;
+    sp.use_cut = 1;
+    sp.cut = p->precision == STENCIL_FP32 ? 154.0f : 1080.0f;
+    return sp;
+}
+
+static cudaError_t alloc_tables(stencil_plan_s* p) {
+    cudaError_t err;
+    int64_t tmax = 4;
+    for (int a = 0; a < p->ndim; ++a) tmax = std::max(tmax, p->dims[a]);
+    p->twn_log2 = ilog2_exact(tmax);
+    const size_t celem = p->precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
+    err = cudaMalloc(&p->tw, celem << p->twn_log2);
+    if (err != cudaSuccess) return err;
+    err = p->precision == STENCIL_FP32 ? launch_twiddles<float>(p->tw, p->twn_log2, 0)
+                                       : launch_twiddles<double>(p->tw, p->twn_log2, 0);
+    if (err != cudaSuccess) return err;
+    for (int a = 0; a < p->ndim; ++a) {
+        err = cudaMalloc(&p->E64[a], sizeof(double2) * p->dims[a]);
+        if (err != cudaSuccess) return err;
+        err = cudaMalloc(&p->E32[a], sizeof(float2) * p->dims[a]);
+        if (err != cudaSuccess) return err;
+        err = launch_axis_table(p->E64[a], p->E32[a], (int)p->dims[a], 0);
+        if (err != cudaSuccess) return err;
+    }
+    err = cudaMalloc(&p->status, sizeof(int));
+    if (err != cudaSuccess) return err;
+    err = cudaMemset(p->status, 0, sizeof(int));
+    return err;
+}
+
+size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision) {
+    if (ndim == 1) return 0;
+    const size_t celem = precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
+    const int64_t n = dims[ndim - 1] / 2;
+    const int64_t align = precision == STENCIL_FP32 ? 16 : 8;
+    const int64_t Mp = (n + 1 + align - 1) / align * align;
+    int64_t rows = 1;
+    for (int a = 0; a < ndim - 1; ++a) rows *= dims[a];
+    return (size_t)rows * (size_t)Mp * celem;
+}
+
+// Periodic solve of `grid` (shape len, the plan's weights) in place, with
+// workspace H (row stride Mp). Used for the whole-grid solve of periodic
+// plans and, in aperiodic.cu, for the interior solve.
+#define PROF_LAUNCH(kind, call)          \
+    do {                                 \
+        p->prof.begin(kind, s);          \
+        err = (call);                    \
+        p->prof.end(s);                  \
+        if (err != cudaSuccess) return err; \
+    } while (0)
+
+template <typename R>
+cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
+                           void* H, long long Mp, const void* tw, int twn_log2,
+                           const double2* const* E64, const float2* const* E32, int* status,
+                           cudaStream_t s) {
+    const int d = p->ndim;
+    const SymbolParams sp = make_symbol_params(p, len, T, E64, E32);
+    const int maxt = sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64;
+    const int celem = 2 * sizeof(R);
+    const int n_log2 = ilog2_exact(len[d - 1]) - 1;
+    const int n = 1 << n_log2;
+    cudaError_t err;
+    if (d == 1) {
+        PROF_LAUNCH(PASS_FUSED_1D, launch_fused_1d<R>(grid, n_log2, 1, tw, twn_log2, sp, status, s));
+        return cudaSuccess;
+    }
+    const int64_t rows = d == 2 ? len[0] : len[0] * len[1];
+    PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_r2c<R>(grid, H, Mp, n_log2, (int)rows, tw, twn_log2, s));
+    if (d == 2) {
+        ColGeom g;
+        g.log2n = ilog2_exact(len[0]);
+        g.S = Mp;
+        g.outer = 1;
+        g.os = 0;
+        g.mid = 1;
+        g.ms = 0;
+        g.inner_valid = n + 1;
+        g.cols_log2 = cols_log2_for(g.log2n, celem, maxt);
+        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, sp, s));
+    } else {
+        ColGeom g1;
+        g1.log2n = ilog2_exact(len[1]);
+        g1.S = Mp;
+        g1.outer = (int)len[0];
+        g1.os = len[1] * Mp;
+        g1.mid = 1;
+        g1.ms = 0;
+        g1.inner_valid = n + 1;
+        g1.cols_log2 = cols_log2_for(g1.log2n, celem, maxt);
+        PROF_LAUNCH(PASS_COLS_FWD, launch_cols<R>(H, g1, -1, tw, twn_log2, s));
+        ColGeom g0;
+        g0.log2n = ilog2_exact(len[0]);
+        g0.S = len[1] * Mp;
+        g0.outer = 1;
+        g0.os = 0;
+        g0.mid = (int)len[1];
+        g0.ms = Mp;
+        g0.inner_valid = n + 1;
+        g0.cols_log2 = cols_log2_for(g0.log2n, celem, maxt);
+        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, sp, s));
+        PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
+    }
+    PROF_LAUNCH(PASS_ROWS_C2R,
+                launch_rows_c2r<R>(H, grid, Mp, n_log2, (int)rows, tw, twn_log2, status, s));
+    return cudaSuccess;
+}
+
+template cudaError_t periodic_solve<float>(stencil_plan_s*, float*, const int64_t*, int64_t,
+                                           void*, long long, const void*, int,
+                                           const double2* const*, const float2* const*, int*,
+                                           cudaStream_t);
+template cudaError_t periodic_solve<double>(stencil_plan_s*, double*, const int64_t*,
+                                            int64_t, void*, long long, const void*, int,
+                                            const double2* const*, const float2* const*, int*,
+                                            cudaStream_t);
+
+}  // namespace sfft
+
+static int from_cuda(cudaError_t err) {
+    if (err == cudaSuccess) return STENCIL_OK;
+    if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
+    return STENCIL_ECUDA;
+}
+
+static void free_plan(stencil_plan_s* p) {
+    if (!p) return;
+    cudaFree(p->tw);
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(p->E64[a]);
+        cudaFree(p->E32[a]);
+    }
+    cudaFree(p->H);
+    cudaFree(p->status);
+    cudaFree(p->dev_grid);
+    aperiodic_release(p);
+    delete p;
+}
+
+extern "C" {
+
+const char* stencil_strerror(int code) {
+    switch (code) {
+        case STENCIL_OK: return "ok";
+        case STENCIL_EINVAL: return "invalid argument";
+        case STENCIL_ENOMEM: return "out of memory";
+        case STENCIL_ECUDA: return "CUDA runtime error";
+        case STENCIL_ETIMEOUT: return "bounded device wait timed out";
+        case STENCIL_ENONFINITE: return "non-finite value in the result";
+        case STENCIL_EQUEUEFULL: return "server queue full";
+        case STENCIL_EUNSUPPORTED: return "unsupported size or option";
+        default: return "unknown status code";
+    }
+}
+
+int64_t stencil_max_axis(int ndim, int precision, int axis) {
+    if (precision != STENCIL_FP32 && precision != STENCIL_FP64) return 0;
+    return max_axis(ndim, precision, axis);
+}
+
+static int validate(int ndim, const int64_t* dims, int radius, int boundary, int precision) {
+    if (ndim < 1 || ndim > 3 || !dims || radius < 0 || radius > kMaxRadius) return STENCIL_EINVAL;
+    if (boundary != STENCIL_PERIODIC && boundary != STENCIL_ZERO_DIRICHLET) return STENCIL_EINVAL;
+    if (precision != STENCIL_FP32 && precision != STENCIL_FP64) return STENCIL_EINVAL;
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 2 * radius + 1 || dims[a] < 4) return STENCIL_EINVAL;
+        if (ilog2_exact(dims[a]) < 0) return STENCIL_EUNSUPPORTED;
+        if (dims[a] > max_axis(ndim, precision, a)) return STENCIL_EUNSUPPORTED;
+    }
+    return STENCIL_OK;
+}
+
+size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int boundary,
+                               int precision) {
+    if (validate(ndim, dims, radius, boundary, precision) != STENCIL_OK) return 0;
+    return periodic_workspace_bytes(ndim, dims, precision);
+}
+
+int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                 const double* weights, int boundary, int precision) {
+    if (!out || !weights) return STENCIL_EINVAL;
+    *out = nullptr;
+    int rc = validate(ndim, dims, radius, boundary, precision);
+    if (rc != STENCIL_OK) return rc;
+    stencil_plan_s* p = new (std::nothrow) stencil_plan_s();
+    if (!p) return STENCIL_ENOMEM;
+    p->ndim = ndim;
+    p->radius = radius;
+    p->boundary = boundary;
+    p->precision = precision;
+    p->nweights = 1;
+    for (int a = 0; a < ndim; ++a) {
+        p->dims[a] = dims[a];
+        p->nweights *= 2 * radius + 1;
+    }
+    for (int i = 0; i < p->nweights; ++i) {
+        if (!std::isfinite(weights[i])) {
+            delete p;
+            return STENCIL_EINVAL;
+        }
+        p->weights[i] = weights[i];
+    }
+    p->real_symbol = symmetric_weights(p->weights, ndim, radius);
+    p->elem = precision == STENCIL_FP32 ? sizeof(float) : sizeof(double);
+    p->n_cells = 1;
+    for (int a = 0; a < ndim; ++a) p->n_cells *= dims[a];
+    cudaGetDevice(&p->device);
+    cudaError_t err = alloc_tables(p);
+    if (err == cudaSuccess) {
+        p->H_bytes = periodic_workspace_bytes(ndim, dims, precision);
+        const int64_t n = dims[ndim - 1] / 2;
+        const int64_t align = precision == STENCIL_FP32 ? 16 : 8;
+        p->Mp = (n + 1 + align - 1) / align * align;
+        if (p->H_bytes) {
+            err = cudaMalloc(&p->H, p->H_bytes);
+            if (err == cudaSuccess) err = cudaMemset(p->H, 0, p->H_bytes);
+        }
+    }
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        free_plan(p);
+        return from_cuda(err);
+    }
+    *out = p;
+    return STENCIL_OK;
+}
+
+int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
+    if (!p || !grid || T < 0) return STENCIL_EINVAL;
+    if (reinterpret_cast<uintptr_t>(grid) % 16) return STENCIL_EINVAL;
+    if (T == 0) return STENCIL_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->boundary == STENCIL_ZERO_DIRICHLET) return aperiodic_run(p, grid, T, s);
+    cudaError_t err;
+    if (p->precision == STENCIL_FP32)
+        err = periodic_solve<float>(p, static_cast<float*>(grid), p->dims, T, p->H, p->Mp, p->tw,
+                                    p->twn_log2, p->E64, p->E32, p->status, s);
+    else
+        err = periodic_solve<double>(p, static_cast<double*>(grid), p->dims, T, p->H, p->Mp, p->tw,
+                                     p->twn_log2, p->E64, p->E32, p->status, s);
+    return from_cuda(err);
+}
+
+int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int64_t T,
+                     void* stream) {
+    if (!p || !host_in || !host_out || T < 0) return STENCIL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)p->n_cells * p->elem;
+    cudaError_t err;
+    if (!p->dev_grid) {
+        err = cudaMalloc(&p->dev_grid, bytes);
+        if (err != cudaSuccess) {
+            p->dev_grid = nullptr;
+            return from_cuda(err);
+        }
+    }
+    err = cudaMemcpyAsync(p->dev_grid, host_in, bytes, cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return from_cuda(err);
+    int rc = stencil_run(p, p->dev_grid, T, stream);
+    if (rc != STENCIL_OK) return rc;
+    err = cudaMemcpyAsync(host_out, p->dev_grid, bytes, cudaMemcpyDeviceToHost, s);
+    if (err != cudaSuccess) return from_cuda(err);
+    return from_cuda(cudaStreamSynchronize(s));
+}
+
+int stencil_symbol_power(stencil_plan_t p, int64_t T, void* out, void* stream) {
+    if (!p || !out || T < 0) return STENCIL_EINVAL;
+    const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32);
+    const int nlast_half = (int)(p->dims[p->ndim - 1] / 2 + 1);
+    long long total = nlast_half;
+    for (int a = 0; a < p->ndim - 1; ++a) total *= p->dims[a];
+    return from_cuda(launch_symbol_table(static_cast<double2*>(out), sp, nlast_half, total,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
+int stencil_status(stencil_plan_t p, void* stream) {
+    if (!p) return STENCIL_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return from_cuda(err);
+    int flag = 0;
+    err = cudaMemcpy(&flag, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return from_cuda(err);
+    if (flag) {
+        err = cudaMemset(p->status, 0, sizeof(int));
+        if (err != cudaSuccess) return from_cuda(err);
+        return STENCIL_ENONFINITE;
+    }
+    return STENCIL_OK;
+}
+
+int stencil_destroy(stencil_plan_t p) {
+    if (!p) return STENCIL_EINVAL;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return STENCIL_OK;
+}
+
+}  // extern "C"
+
+extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
+    if (!p || (cutoff != 0 && cutoff < 2)) return STENCIL_EINVAL;
+    p->cutoff = cutoff;
+    return STENCIL_OK;
+}
+
+static const char* kPassNames[PASS_KINDS] = {
+    "rows_r2c", "cols_fwd", "cols_fused", "cols_inv", "rows_c2r", "fused_1d",
+    "strip_r2c", "strip_cols", "strip_c2r", "base_loop", "copy"};
+
+extern "C" int stencil_profile_enable(stencil_plan_t p, int enable) {
+    if (!p) return STENCIL_EINVAL;
+    p->prof.enabled = enable != 0;
+    return STENCIL_OK;
+}
+
+extern "C" int stencil_profile_read(stencil_plan_t p, double* ms, int64_t* launches, int nkinds) {
+    if (!p || !ms || !launches || nkinds < 0) return STENCIL_EINVAL;
+    cudaError_t err = p->prof.collect();
+    for (int k = 0; k < nkinds && k < PASS_KINDS; ++k) {
+        ms[k] = p->prof.ms[k];
+        launches[k] = p->prof.launches[k];
+        p->prof.ms[k] = 0.0;
+        p->prof.launches[k] = 0;
+    }
+    for (int k = PASS_KINDS; k < nkinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    return from_cuda(err);
+}
+
+extern "C" const char* stencil_profile_kind_name(int kind) {
+    if (kind < 0 || kind >= PASS_KINDS) return nullptr;
+    return kPassNames[kind];
+}

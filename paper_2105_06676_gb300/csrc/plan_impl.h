@@ -1,0 +1,91 @@
+// The plan object behind the opaque stencil_plan_t handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.h"
+
+struct AperiodicState;
+
+// Kernel kinds for per-pass timing (stencil_profile_*).
+enum PassKind {
+    PASS_ROWS_R2C = 0,
+    PASS_COLS_FWD = 1,
+    PASS_COLS_FUSED = 2,
+    PASS_COLS_INV = 3,
+    PASS_ROWS_C2R = 4,
+    PASS_FUSED_1D = 5,
+    PASS_STRIP_R2C = 6,
+    PASS_STRIP_COLS = 7,
+    PASS_STRIP_C2R = 8,
+    PASS_BASE_LOOP = 9,
+    PASS_COPY = 10,
+    PASS_KINDS = 11
+};
+
+// Optional CUDA-event bracketing of every kernel launch of a run, on the
+// launching stream.
+struct Profiler {
+    bool enabled = false;
+    struct Mark { int kind; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    double ms[PASS_KINDS] = {};
+    long long launches[PASS_KINDS] = {};
+    cudaEvent_t get();
+    void begin(int kind, cudaStream_t s);
+    void end(cudaStream_t s);
+    cudaError_t collect();
+    ~Profiler();
+};
+
+struct stencil_plan_s {
+    int ndim = 0;
+    int radius = 0;
+    int boundary = 0;
+    int precision = 0;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t n_cells = 0;
+    double weights[sfft::kMaxWeights] = {};
+    int nweights = 0;
+    bool real_symbol = false;
+    size_t elem = 0;
+    int device = 0;
+    // twiddles exp(-2 pi i m / 2^twn_log2) at pass precision
+    int twn_log2 = 0;
+    void* tw = nullptr;
+    // per-axis exp(+2 pi i q / l_a), FP64 and FP32
+    double2* E64[3] = {nullptr, nullptr, nullptr};
+    float2* E32[3] = {nullptr, nullptr, nullptr};
+    // half-spectrum workspace of the whole-grid solve
+    void* H = nullptr;
+    long long Mp = 0;
+    size_t H_bytes = 0;
+    // latched device status (bit 0: non-finite output)
+    int* status = nullptr;
+    // device grid owned by stencil_run_host
+    void* dev_grid = nullptr;
+    // zero-Dirichlet schedule and buffers (aperiodic.cu)
+    AperiodicState* ap = nullptr;
+    int64_t cutoff = 0;  // 0: automatic
+    Profiler prof;
+};
+
+namespace sfft {
+int ilog2_exact(int64_t v);
+int64_t max_axis(int ndim, int precision, int axis);
+SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
+                                const double2* const* E64, const float2* const* E32);
+size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision);
+template <typename R>
+cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
+                           void* H, long long Mp, const void* tw, int twn_log2,
+                           const double2* const* E64, const float2* const* E32, int* status,
+                           cudaStream_t s);
+}  // namespace sfft
+
+int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
+void aperiodic_release(stencil_plan_s* p);

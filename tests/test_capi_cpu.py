@@ -1,0 +1,127 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/*.h declares, and rejects bad arguments before any
+CUDA call."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_2105_06676_gb300 import _capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return _capi.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(stencil_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_core_entry_points():
+    names = declared_functions()
+    for core in ("stencil_plan", "stencil_run", "stencil_destroy", "stencil_status",
+                 "stencil_strerror", "stencil_symbol_power", "stencil_run_host"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    bound = {name for name, _, _ in _capi.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_strerror_names_every_code(lib):
+    for code, name in _capi.STATUS.items():
+        msg = lib.stencil_strerror(code)
+        assert msg and msg.decode() != "unknown status code", name
+    assert lib.stencil_strerror(12345).decode() == "unknown status code"
+
+
+def _plan(lib, dims, radius, boundary=0, precision=1, weights=None):
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    if weights is None:
+        weights = np.full(max(1, 2 * radius + 1) ** len(dims), 0.1)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    h = ctypes.c_void_p()
+    rc = lib.stencil_plan(ctypes.byref(h), len(dims), d, radius,
+                          w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), boundary, precision)
+    return rc, h
+
+
+@pytest.mark.parametrize("dims,radius,boundary,precision,code", [
+    ((), 1, 0, 1, -1),                  # ndim 0
+    ((8, 8, 8, 8), 1, 0, 1, -1),        # ndim 4
+    ((16,), -1, 0, 1, -1),              # negative radius
+    ((16,), 4, 0, 1, -1),               # radius above the supported maximum
+    ((16,), 1, 2, 1, -1),               # unknown boundary
+    ((16,), 1, 0, 7, -1),               # unknown precision
+    ((2,), 0, 0, 1, -1),                # axis shorter than 4
+    ((4,), 2, 0, 1, -1),                # axis shorter than 2r+1
+    ((12,), 1, 0, 1, -7),               # not a power of two
+    ((1 << 20,), 1, 0, 1, -7),          # beyond the single-CTA 1-D limit
+])
+def test_plan_rejects_bad_arguments(lib, dims, radius, boundary, precision, code):
+    if len(dims) == 0:
+        h = ctypes.c_void_p()
+        w = np.zeros(3)
+        rc = lib.stencil_plan(ctypes.byref(h), 0, (ctypes.c_int64 * 1)(8), 1,
+                              w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 1)
+    else:
+        rc, h = _plan(lib, dims, radius, boundary, precision)
+    assert rc == code
+    assert not h.value
+
+
+def test_plan_rejects_null_and_nonfinite(lib):
+    d = (ctypes.c_int64 * 1)(16)
+    w = np.array([0.25, 0.5, 0.25])
+    wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.stencil_plan(None, 1, d, 1, wp, 0, 1) == -1
+    h = ctypes.c_void_p()
+    assert lib.stencil_plan(ctypes.byref(h), 1, d, 1, None, 0, 1) == -1
+    bad = np.array([0.25, np.nan, 0.25])
+    assert lib.stencil_plan(ctypes.byref(h), 1, d, 1,
+                            bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 1) == -1
+
+
+def test_null_plan_calls_are_rejected(lib):
+    assert lib.stencil_run(None, None, 1, None) == -1
+    assert lib.stencil_run_host(None, None, None, 1, None) == -1
+    assert lib.stencil_status(None, None) == -1
+    assert lib.stencil_destroy(None) == -1
+    assert lib.stencil_symbol_power(None, 1, None, None) == -1
+    assert lib.stencil_plan_set_cutoff(None, 8) == -1
+    assert lib.stencil_profile_enable(None, 1) == -1
+
+
+def test_size_limits_and_workspace(lib):
+    assert lib.stencil_max_axis(2, 1, 1) >= 8192
+    assert lib.stencil_max_axis(2, 1, 0) >= 8192
+    assert lib.stencil_max_axis(4, 1, 0) == 0
+    d = (ctypes.c_int64 * 2)(4096, 4096)
+    # half spectrum 4096 x (2048 + 1 padded to 2064) complex float
+    assert lib.stencil_workspace_bytes(2, d, 1, 0, 1) == 4096 * 2064 * 8
+    d1 = (ctypes.c_int64 * 1)(4096)
+    assert lib.stencil_workspace_bytes(1, d1, 1, 0, 0) == 0
+    assert lib.stencil_profile_kind_name(0).decode() == "rows_r2c"
+    assert lib.stencil_profile_kind_name(999) is None

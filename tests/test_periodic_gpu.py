@@ -1,0 +1,219 @@
+"""Parity of the periodic CUDA path (StencilFFT-P) with the CPU oracle.
+
+Tolerance (relative to max|a_0|): 1e-10 for FP64 plans, 2e-4 for FP32 plans.
+Small and medium cases compare every element with the nested-loop oracle;
+the full-size grids compare with the oracle's numpy StencilFFT-P (itself pinned
+to the loop) and with closed forms that hold at any size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06676_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 2e-4}
+
+
+def run_gpu(a0, w, T, precision, boundary="periodic", cutoff=None):
+    from paper_2105_06676_gb300 import StencilPlan
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(a0.shape, w, boundary, precision)
+    if cutoff is not None:
+        plan.set_cutoff(cutoff)
+    plan.run(g, T)
+    rc = plan.status()
+    plan.close()
+    assert rc == 0, f"device status {rc}"
+    return g.double().cpu().numpy()
+
+
+def err_rel(got, ref, a0):
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(a0)))
+
+
+SMALL = [
+    ((4,), "sym", 1), ((8,), "asym", 1), ((64,), "sym", 1), ((256,), "asym", 2), ((4096,), "sym", 1),
+    ((8, 8), "sym", 1), ((16, 32), "asym", 1), ((64, 128), "asym", 2), ((256, 64), "sym", 1),
+    ((128, 16), "asym", 1), ((8, 8, 8), "sym", 1), ((16, 8, 32), "asym", 1), ((32, 32, 16), "asym", 2),
+]
+
+
+def weights_for(ndim, kind, r, seed):
+    if kind == "sym":
+        w = wl.weights_random_box(ndim, r, seed)
+        return 0.5 * (w + np.flip(w))            # symmetric under m -> -m: real symbol
+    return wl.weights_random_box(ndim, r, seed)  # general: complex symbol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims,kind,r", SMALL)
+@pytest.mark.parametrize("T", [1, 2, 3, 7, 64, 1000])
+def test_periodic_matches_loop(dims, kind, r, T, precision):
+    if max(dims) < 2 * r + 1:
+        pytest.skip("grid smaller than the stencil")
+    n = int(np.prod(dims))
+    if n * T > 3e8:
+        pytest.skip("loop oracle too slow for this combination")
+    w = weights_for(len(dims), kind, r, 11 + T)
+    a0 = wl.grid_uniform(dims, 5 + T)
+    ref = oracle.stencil_loop(a0, w, T)
+    got = run_gpu(a0, w, T, precision)
+    assert err_rel(got, ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_T_zero_leaves_grid_unchanged(precision):
+    a0 = wl.grid_uniform((32, 16), 3)
+    got = run_gpu(a0, wl.weights_star(2, 0.6, 0.1), 0, precision)
+    np.testing.assert_array_equal(got, a0.astype(np.float32 if precision == "fp32" else np.float64))
+
+
+def test_worked_example_symbol_and_matrix():
+    # appendix "Stencil Matrix Example": weights (-2, 1, 3) on 4 cells
+    from paper_2105_06676_gb300 import StencilPlan
+    w = np.array([-2.0, 1.0, 3.0])
+    plan = StencilPlan((4,), w, "periodic", "fp64")
+    lam = plan.symbol_power(1).cpu().numpy()
+    np.testing.assert_allclose(lam, [2, 1 + 5j, 0], atol=1e-14)
+    lam3 = plan.symbol_power(3).cpu().numpy()
+    np.testing.assert_allclose(lam3, np.array([2, 1 + 5j, 0]) ** 3, atol=1e-12)
+    plan.close()
+    S = np.stack([run_gpu(np.eye(4)[j], w, 1, "fp64") for j in range(4)], axis=1)
+    np.testing.assert_allclose(S, [[1, 3, 0, -2], [-2, 1, 3, 0], [0, -2, 1, 3], [3, 0, -2, 1]],
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,r", [((64,), 1), ((16, 32), 2), ((8, 16, 32), 1), ((4096, 64), 1)])
+@pytest.mark.parametrize("T", [0, 1, 5, 1000, 10000])
+def test_symbol_power_table_matches_oracle(dims, r, T):
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_signed(len(dims), r, 3 + T) * 0.4
+    plan = StencilPlan(dims, w, "periodic", "fp64")
+    got = plan.symbol_power(T).cpu().numpy()
+    plan.close()
+    lam = oracle.symbol_closed_form(w, dims)
+    half = lam[..., : dims[-1] // 2 + 1]
+    ref = oracle.symbol_power(half, T)
+    # first-order error bound of a T-th power: T |lam|^(T-1) |d lam| + T eps |lam|^T,
+    # with |d lam| <= eps * sum|w| * (number of terms)
+    eps = np.finfo(np.float64).eps
+    a = np.abs(half)
+    dlam = 16 * eps * np.abs(w).sum()
+    bound = (max(T, 1) * (a ** max(T - 1, 0) * dlam + 16 * eps * a ** T)) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+# -------------------------------------------------------------------------
+# full-size grids of the benchmark workloads
+# -------------------------------------------------------------------------
+def test_heat1d_4096_full_size_fp64():
+    wk = wl.heat1d_4096()
+    a0 = wk.grid()
+    ref = oracle.stencil_loop(a0, wk.weights, wk.T)
+    got = run_gpu(a0, wk.weights, wk.T, "fp64")
+    assert err_rel(got, ref, a0) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_star2d_4096_full_size_vs_spectral_oracle(precision):
+    wk = wl.star2d_4096(precision)
+    a0, ks, amps = wl.grid_with_modes(wk.dims, wk.grid_seed, 3002)
+    for T in (1, 10, 100, wk.T):
+        ref = oracle.stencil_fft_periodic(a0, wk.weights, T)
+        got = run_gpu(a0, wk.weights, T, precision)
+        assert err_rel(got, ref, a0) <= TOL[precision], T
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_star2d_4096_fourier_modes_closed_form(precision):
+    # a pure mode sin(k.x) scales by lambda(k)^T with lambda = 0.6 + 0.2 cos + 0.2 cos
+    wk = wl.star2d_4096(precision)
+    l = wk.dims[0]
+    ks, _ = wl.seeded_modes(2, 3002)
+    for k in ks + [(l // 2, l // 2), (64, 0)]:
+        a0 = wl.fourier_mode(wk.dims, k, 0.2)
+        lam = 0.6 + 0.2 * np.cos(2 * np.pi * k[0] / l) + 0.2 * np.cos(2 * np.pi * k[1] / l)
+        got = run_gpu(a0, wk.weights, wk.T, precision)
+        assert err_rel(got, lam ** wk.T * a0, a0) <= TOL[precision], k
+
+
+def test_star2d_4096_T1_loop_sample_fp32():
+    wk = wl.star2d_4096("fp32")
+    a0 = wk.grid()
+    ref = oracle.stencil_loop(a0, wk.weights, 3)
+    got = run_gpu(a0, wk.weights, 3, "fp32")
+    assert err_rel(got, ref, a0) <= 2e-4
+
+
+def test_star2d_mass_conservation_fp32():
+    wk = wl.star2d_4096("fp32")
+    a0 = wk.grid()
+    got = run_gpu(a0, wk.weights, wk.T, "fp32")
+    assert abs(got.mean() - a0.astype(np.float32).astype(np.float64).mean()) < 2e-4
+
+
+def test_star3d_512_full_size_fp32():
+    wk = wl.star3d_512("fp32")
+    a0 = wk.grid()
+    # T = 2 against the loop on the full grid
+    ref = oracle.stencil_loop(a0, wk.weights, 2)
+    got = run_gpu(a0, wk.weights, 2, "fp32")
+    assert err_rel(got, ref, a0) <= 2e-4
+    # T = 1000 on pure modes (closed form) and the mean (mass)
+    l = wk.dims[0]
+    for k in [(1, 2, 3), (5, 0, 9), (256, 256, 256)]:
+        m = wl.fourier_mode(wk.dims, k, 0.3)
+        lam = 0.4 + sum(0.2 * np.cos(2 * np.pi * kk / l) for kk in k)
+        gotm = run_gpu(m, wk.weights, wk.T, "fp32")
+        assert err_rel(gotm, lam ** wk.T * m, m) <= 2e-4, k
+    full = run_gpu(a0, wk.weights, wk.T, "fp32")
+    assert abs(full.mean() - a0.mean()) < 2e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_run_host_matches_device_run(precision):
+    from paper_2105_06676_gb300 import StencilPlan
+    dims, T = (256, 128), 77
+    w = wl.weights_random_box(2, 1, 9)
+    a0 = wl.grid_uniform(dims, 4)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plan = StencilPlan(dims, w, "periodic", precision)
+    host = torch.tensor(a0, dtype=dt).pin_memory()
+    out = plan.run_host(host, T)
+    dev = torch.tensor(a0, dtype=dt, device="cuda")
+    plan.run(dev, T)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.numpy(), dev.cpu().numpy())
+    plan.close()
+
+
+def test_nonfinite_output_is_reported():
+    from paper_2105_06676_gb300 import StencilPlan
+    dims = (64, 64)
+    w = wl.weights_star(2, 3.0, 1.0)          # |lambda| up to 7: lambda^T overflows
+    plan = StencilPlan(dims, w, "periodic", "fp32")
+    g = torch.ones(dims, dtype=torch.float32, device="cuda")
+    plan.run(g, 100000)
+    assert plan.status() == -5
+    assert plan.status() == 0                 # latch cleared
+    plan.close()
+
+
+def test_profile_counts_launches():
+    from paper_2105_06676_gb300 import StencilPlan
+    dims = (128, 256)
+    plan = StencilPlan(dims, wl.weights_star(2, 0.6, 0.1), "periodic", "fp32")
+    g = torch.tensor(wl.grid_uniform(dims, 1), dtype=torch.float32, device="cuda")
+    plan.profile(True)
+    for _ in range(3):
+        plan.run(g, 10)
+    prof = plan.profile_read()
+    assert {k: v[1] for k, v in prof.items()} == {"rows_r2c": 3, "cols_fused": 3, "rows_c2r": 3}
+    assert all(v[0] > 0 for v in prof.values())
+    plan.close()
