@@ -234,6 +234,18 @@ def main():
     times64 = time_solve(plan64, g64, pristine64, flush, max(3, args.steps // 4), 3, T)
     ms64 = sum(times64) / len(times64)
 
+    # ---- zero-Dirichlet path (secondary): 8192^2 9-point box, T = 4096, FP32
+    wd = wl.box2d_8192_dirichlet()
+    ad = wd.grid()
+    pland = StencilPlan(wd.dims, wd.weights, "dirichlet", "fp32")
+    pris_d = torch.tensor(ad, dtype=torch.float32, device="cuda")
+    gd = pris_d.clone()
+    times_d = time_solve(pland, gd, pris_d, flush, 2, 1, wd.T)
+    ms_d = sum(times_d) / len(times_d)
+    assert pland.status() == 0
+    del gd, pris_d
+    pland.close()
+
     # ---- e2e through the C ABI with pinned host buffers (H2D + solve + D2H per step)
     host_in = torch.tensor(a0, dtype=torch.float32).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -285,6 +297,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed (512 MiB write) between timed steps; grid restored outside the events"},
             "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64},
+            "dirichlet_path": {"workload": wd.name, "value": world * wd.n_cells * wd.T / (ms_d * 1e-3),
+                               "ms_per_step": ms_d},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": grid_bytes,
                     "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,

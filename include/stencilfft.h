@@ -142,6 +142,25 @@ int stencil_profile_enable(stencil_plan_t plan, int enable);
 int stencil_profile_read(stencil_plan_t plan, double* ms, int64_t* launches, int nkinds);
 const char* stencil_profile_kind_name(int kind);
 
+/*
+ * Host-only view of the zero-Dirichlet schedule (RecursiveBoundary flattened
+ * into a sequence of operations, paper Fig.
+ * "stencil-fft-algorithm-1D-aperiodic"), for checking the schedule without a
+ * GPU. Writes up to cap int64 values to out (may be NULL) and returns the
+ * number needed, or -1 for invalid arguments (radius must be >= 1, T >= 1).
+ * Records, in execution order:
+ *   1, step, T_k, level, n, then per strip: bdims[3], off[3], valid[3], lo, hi,
+ *      face_axis, face_side            -- periodic solves of the strips (stashed)
+ *   2, step                            -- scatter of that step's kept cells
+ *   3, T_b, n, then per tile: (lo, hi) for each of 3 axes
+ *                                      -- base case over output tiles
+ * Axes beyond ndim are reported with extent 1. A strip's box cell q maps to
+ * grid cell off + q when q < valid on every axis; a scatter writes the cells
+ * with lo < dist <= hi and, when face_axis >= 0, distance to that face <= hi.
+ */
+int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_t T,
+                               int64_t cutoff, int64_t* out, int64_t cap);
+
 /* Release a plan and all its device memory (synchronises the device). */
 int stencil_destroy(stencil_plan_t plan);
 

@@ -114,6 +114,8 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
     double N = 1.0;
     for (int a = 0; a < p->ndim; ++a) {
         sp.len[a] = (int)len[a];
+        sp.tshift[a] = ilog2_exact(p->dims[a]) - ilog2_exact(len[a]);
+        sp.tmask[a] = (int)(len[a] - 1);
         N *= (double)len[a];
         sp.E64[a] = E64[a];
         sp.E32[a] = E32[a];

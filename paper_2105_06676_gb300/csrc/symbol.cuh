@@ -34,7 +34,9 @@ struct SymbolParams {
     int use_cut;
     float delta;           // bound on |Lambda - Lambda_fp32|
     float cut;             // skip when T log2(|Lambda_fp32| + delta) < -cut
-    int len[3];            // axis lengths l_a (full lengths, also for the halved last axis)
+    int len[3];            // axis lengths l_a of the solved box (full length of the halved last axis)
+    int tshift[3];         // tables hold exp(2 pi i q / (l_a << tshift)): index scale of this box
+    int tmask[3];          // l_a - 1
     const double2* E64[3];
     const float2* E32[3];
     double w[kMaxWeights];
@@ -49,18 +51,16 @@ __device__ __forceinline__ C lambda_eval_r(const SymbolParams& p, const C* const
                                            const int* k) {
     constexpr int W = 2 * RAD + 1;
     C e0[W], e1[W], e2[W];
-    const int m0 = p.len[0] - 1;
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e0[m + RAD] = __ldg(E[0] + ((m * k[0]) & m0));
+    for (int m = -RAD; m <= RAD; ++m) e0[m + RAD] = __ldg(E[0] + (((m * k[0]) & p.tmask[0]) << p.tshift[0]));
     if (p.ndim == 1) {
         C acc{0, 0};
 #pragma unroll
         for (int i = 0; i < W; ++i) acc = cadd(acc, cscale(e0[i], w[i]));
         return acc;
     }
-    const int m1 = p.len[1] - 1;
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e1[m + RAD] = __ldg(E[1] + ((m * k[1]) & m1));
+    for (int m = -RAD; m <= RAD; ++m) e1[m + RAD] = __ldg(E[1] + (((m * k[1]) & p.tmask[1]) << p.tshift[1]));
     if (p.ndim == 2) {
         C acc{0, 0};
 #pragma unroll
@@ -72,9 +72,8 @@ __device__ __forceinline__ C lambda_eval_r(const SymbolParams& p, const C* const
         }
         return acc;
     }
-    const int m2 = p.len[2] - 1;
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e2[m + RAD] = __ldg(E[2] + ((m * k[2]) & m2));
+    for (int m = -RAD; m <= RAD; ++m) e2[m + RAD] = __ldg(E[2] + (((m * k[2]) & p.tmask[2]) << p.tshift[2]));
     C acc{0, 0};
 #pragma unroll
     for (int i = 0; i < W; ++i) {

@@ -93,7 +93,8 @@ def test_worked_example_symbol_and_matrix():
 @pytest.mark.parametrize("T", [0, 1, 5, 1000, 10000])
 def test_symbol_power_table_matches_oracle(dims, r, T):
     from paper_2105_06676_gb300 import StencilPlan
-    w = wl.weights_random_signed(len(dims), r, 3 + T) * 0.4
+    w = wl.weights_random_signed(len(dims), r, 3 + T)
+    w = w / np.abs(w).sum()                   # |lambda| <= 1: lambda^T stays finite
     plan = StencilPlan(dims, w, "periodic", "fp64")
     got = plan.symbol_power(T).cpu().numpy()
     plan.close()

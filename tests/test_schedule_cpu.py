@@ -1,0 +1,171 @@
+"""Host-side check of the zero-Dirichlet schedule (no GPU).
+
+The library exports the RecursiveBoundary schedule it would launch
+(stencil_debug_schedule). This test executes that schedule with numpy
+stand-ins for each kernel -- gather, periodic solve of a strip box (the
+oracle's StencilFFT-P), masked scatter, temporally blocked base-case tiles
+(the oracle's loop on the tile's input box) -- and compares the result with
+the zero-Dirichlet loop oracle. A wrong strip width, keep range, offset,
+face mask, odd-T split or base-tile cover fails here on the CPU.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+from paper_2105_06676_gb300 import _capi
+from paper_2105_06676_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return _capi.lib()
+
+
+def fetch_schedule(lib, dims, r, T, cutoff):
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    n = lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, None, 0)
+    assert n > 0
+    buf = (ctypes.c_int64 * n)()
+    assert lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, buf, n) == n
+    return list(buf)
+
+
+def decode(v):
+    ops, i = [], 0
+    while i < len(v):
+        kind = v[i]
+        if kind == 1:
+            step, Tk, level, n = v[i + 1:i + 5]
+            i += 5
+            strips = []
+            for _ in range(n):
+                f = v[i:i + 13]
+                i += 13
+                strips.append(dict(bdims=f[0:3], off=f[3:6], valid=f[6:9], lo=f[9], hi=f[10],
+                                   face_axis=f[11], face_side=f[12]))
+            ops.append(("solve", step, Tk, level, strips))
+        elif kind == 2:
+            ops.append(("scatter", v[i + 1]))
+            i += 2
+        elif kind == 3:
+            Tb, n = v[i + 1], v[i + 2]
+            i += 3
+            tiles = []
+            for _ in range(n):
+                f = v[i:i + 6]
+                i += 6
+                tiles.append((f[0::2], f[1::2]))
+            ops.append(("base", Tb, tiles))
+        else:
+            raise AssertionError(f"bad op {kind}")
+    return ops
+
+
+def emulate(a0, w, T, ops):
+    dims = a0.shape
+    nd = a0.ndim
+    r = (w.shape[0] - 1) // 2
+    dist = oracle.boundary_distance(dims)
+    X = a0.copy()
+    maxdist = min(l // 2 for l in dims)
+    Z = oracle.stencil_fft_periodic(a0, w, T) if r * T < maxdist else None
+    stash = {}
+    grids = np.meshgrid(*[np.arange(l) for l in dims], indexing="ij")
+    for op in ops:
+        if op[0] == "solve":
+            _, step, Tk, level, strips = op
+            out = []
+            for s in strips:
+                bd = tuple(s["bdims"][:nd])
+                S = np.zeros(bd)
+                sl_box = tuple(slice(0, s["valid"][a]) for a in range(nd))
+                sl_grid = tuple(slice(s["off"][a], s["off"][a] + s["valid"][a]) for a in range(nd))
+                S[sl_box] = X[sl_grid]
+                out.append(oracle.stencil_fft_periodic(S, w, Tk))
+            stash[step] = (strips, out)
+        elif op[0] == "scatter":
+            strips, out = stash.pop(op[1])
+            for s, S in zip(strips, out):
+                sl_box = tuple(slice(0, s["valid"][a]) for a in range(nd))
+                sl_grid = tuple(slice(s["off"][a], s["off"][a] + s["valid"][a]) for a in range(nd))
+                m = (dist[sl_grid] > s["lo"]) & (dist[sl_grid] <= s["hi"])
+                fa = s["face_axis"]
+                if fa >= 0:
+                    g = grids[fa][sl_grid]
+                    df = g + 1 if s["face_side"] == 0 else dims[fa] - g
+                    m &= df <= s["hi"]
+                sub = X[sl_grid]
+                sub[m] = S[sl_box][m]
+        else:
+            _, Tb, tiles = op
+            h = r * Tb
+            Y = X.copy()
+            for lo, hi in tiles:
+                lo, hi = lo[:nd], hi[:nd]
+                ilo = [max(lo[a] - h, 0) for a in range(nd)]
+                ihi = [min(hi[a] + h, dims[a]) for a in range(nd)]
+                sub = X[tuple(slice(ilo[a], ihi[a]) for a in range(nd))]
+                res = oracle.stencil_loop(sub, w, Tb, "dirichlet")
+                osl = tuple(slice(lo[a], hi[a]) for a in range(nd))
+                rsl = tuple(slice(lo[a] - ilo[a], hi[a] - ilo[a]) for a in range(nd))
+                m = dist[osl] <= r * Tb
+                Y[osl][m] = res[rsl][m]
+            cover = dist <= r * Tb
+            X[cover] = Y[cover]
+    if Z is not None:
+        X[dist > r * T] = Z[dist > r * T]
+    return X
+
+
+CASES = [
+    ((64,), 1, T, c) for T in (1, 2, 3, 5, 7, 13, 19, 40) for c in (2, 3, 8)
+] + [
+    ((256,), 2, 50, 4), ((64,), 2, 45, 0), ((32,), 1, 45, 2), ((1024,), 1, 300, 0),
+    ((32, 32), 1, 9, 2), ((32, 16), 1, 13, 3), ((64, 32), 2, 6, 2), ((16, 64), 1, 11, 4),
+    ((64, 64), 1, 32, 0), ((128, 64), 1, 40, 8), ((16, 16, 16), 1, 5, 2), ((32, 16, 8), 1, 7, 3),
+    ((16, 16, 32), 1, 10, 0),
+]
+
+
+@pytest.mark.parametrize("dims,r,T,cutoff", CASES)
+def test_schedule_reproduces_dirichlet_loop(lib, dims, r, T, cutoff):
+    w = wl.weights_random_box(len(dims), r, 100 + T)
+    a0 = wl.grid_uniform(dims, 7 + T)
+    ops = decode(fetch_schedule(lib, dims, r, T, cutoff))
+    got = emulate(a0, w, T, ops)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(a0)) < 1e-11
+
+
+def test_schedule_structure(lib):
+    ops = decode(fetch_schedule(lib, (8192, 8192), 1, 4096, 32))
+    solves = [o for o in ops if o[0] == "solve"]
+    bases = [o for o in ops if o[0] == "base"]
+    # T = 4096 halves down to 16 < 32: 256 leaves, 255 internal nodes x 2 solves
+    assert len(bases) == 256 and len(solves) == 510
+    assert all(o[1] == 16 for o in bases)
+    # the top two levels are whole-grid solves, deeper ones four face strips
+    assert all(len(o[4]) == 1 for o in solves if o[3] <= 1)
+    assert all(len(o[4]) == 4 for o in solves if o[3] >= 2)
+    # every scatter follows its solve
+    seen = set()
+    for o in ops:
+        if o[0] == "solve":
+            seen.add(o[1])
+        elif o[0] == "scatter":
+            assert o[1] in seen
+
+
+def test_schedule_rejects_bad_arguments(lib):
+    d = (ctypes.c_int64 * 1)(64)
+    assert lib.stencil_debug_schedule(1, d, 0, 5, 0, None, 0) == -1
+    assert lib.stencil_debug_schedule(1, d, 1, 0, 0, None, 0) == -1
+    assert lib.stencil_debug_schedule(1, d, 1, 5, 1, None, 0) == -1
+    d12 = (ctypes.c_int64 * 1)(12)
+    assert lib.stencil_debug_schedule(1, d12, 1, 5, 0, None, 0) == -1
