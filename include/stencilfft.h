@@ -161,6 +161,31 @@ const char* stencil_profile_kind_name(int kind);
 int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_t T,
                                int64_t cutoff, int64_t* out, int64_t cap);
 
+/*
+ * Periodic solve that allocates nothing. The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory when they
+ * solve (a latency-critical loop that cannot pay cudaMalloc's implicit device
+ * synchronisation, or a program whose allocator has already reserved the
+ * device memory). It advances grid (device pointer, 16-byte aligned, prod(dims)
+ * elements of the given precision) by T >= 0 steps in place on stream, exactly
+ * like stencil_plan + stencil_run with STENCIL_PERIODIC, but takes all scratch
+ * (tables, half-spectrum workspace, status word) from one fixed device array of
+ * stencil_noalloc_scratch_bytes() bytes (32 MiB) that every GPU loading this
+ * library holds until exit. Sizes whose scratch does not fit return
+ * STENCIL_EUNSUPPORTED (e.g. a 2-D FP32 grid holds up to 2048 x 2048 cells);
+ * bad arguments return STENCIL_EINVAL. The first call on a device sets that
+ * device up (looks up the array's address) and should come before any stream
+ * capture. Calls share the array: calls whose work overlaps on the GPU race and
+ * must be serialised by the caller. Non-finite output is not reported. Calls no
+ * allocating routine.
+ */
+int stencil_periodic_run_noalloc(int ndim, const int64_t* dims, int radius,
+                                 const double* weights, int precision, void* grid,
+                                 int64_t T, void* stream);
+
+/* Size in bytes of the fixed scratch array used by stencil_periodic_run_noalloc. */
+size_t stencil_noalloc_scratch_bytes(void);
+
 /* Release a plan and all its device memory (synchronises the device). */
 int stencil_destroy(stencil_plan_t plan);
 

@@ -41,6 +41,9 @@ SIGNATURES = [
     ("stencil_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("stencil_profile_read", _c.c_int, [_vp, _c.POINTER(_c.c_double), _i64p, _c.c_int]),
     ("stencil_profile_kind_name", _c.c_char_p, [_c.c_int]),
+    ("stencil_periodic_run_noalloc", _c.c_int, [_c.c_int, _i64p, _c.c_int, _dp, _c.c_int, _vp,
+                                                 _c.c_int64, _vp]),
+    ("stencil_noalloc_scratch_bytes", _c.c_size_t, []),
     ("stencil_debug_schedule", _c.c_int64, [_c.c_int, _i64p, _c.c_int, _c.c_int64, _c.c_int64,
                                             _i64p, _c.c_int64]),
 ]
