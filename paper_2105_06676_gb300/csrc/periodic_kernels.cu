@@ -17,6 +17,9 @@
 // V is evaluated at the natural frequency of each element.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
+#include "fft_reg.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -283,6 +286,217 @@ __global__ void k_symbol_table(double2* out, const __grid_constant__ SymbolParam
 }
 
 // ---------------------------------------------------------------------------
+// register-resident kernels (transform length n >= 16): q = n/16 threads per
+// sequence, 16 elements per thread, two shared-memory exchanges per 4096-point
+// transform instead of a shared-memory round trip per stage
+// ---------------------------------------------------------------------------
+template <typename R, int RAD, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
+               const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
+               const __grid_constant__ SymbolParams p, int* status) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2, q = n >> 4;
+    const int ss = seq_stride(n);
+    const int c = threadIdx.x / q, j = threadIdx.x - c * q;
+    const int row = blockIdx.x * rpc + c;
+    const bool live = row < nrows;
+    const SeqView<C> sm{small + c * ss};
+    C* rowp = reinterpret_cast<C*>(grid) + (size_t)(live ? row : 0) * n;
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? rowp[j + q * s] : C{0, 0};
+    reg_fft<-1>(v, sm, j, n_log2, tw, twn_log2);
+    // real-input split: X[k] from Z[k] and Z[n-k]
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+    __syncthreads();
+    const int sh = twn_log2 - n_log2 - 1;  // W^k = exp(-2 pi i k / 2n) = tw[k << sh]
+    C xn{0, 0};                             // X[n], thread j = 0 only
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = j + q * r;
+        const C zk = v[r];
+        const C znk = sm[(n - k) & (n - 1)];
+        const C xe = cscale(cadd(zk, cconj(znk)), (R)0.5);
+        const C xo = cscale(cmul_mi(csub(zk, cconj(znk))), (R)0.5);
+        const C t = cmul(tw[k << sh], xo);
+        v[r] = cadd(xe, t);
+        if (k == 0) xn = csub(xe, xo);
+    }
+    __syncthreads();
+    // Y[k] = V[k] X[k]
+    ColSymbol<RAD> cs;
+    int kz[3] = {0, 0, 0};
+    col_symbol_init<RAD>(p, kz, cs);
+    apply_multiplier<RAD>(v, sm, j, q, p, cs, 0, 0);
+    if (j == 0) xn = multiply_single<C>(xn, p, n, 0, 0);
+    __syncthreads();
+    // inverse split: Z'[k] = (Y[k] + conj Y[n-k]) + i conj(W^k) (Y[k] - conj Y[n-k])
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+    if (j == 0) sm[n] = xn;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = j + q * r;
+        const C yk = v[r];
+        const C ynk = sm[n - k];
+        const C wk = tw[k << sh];
+        v[r] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
+    }
+    __syncthreads();
+    reg_fft<+1>(v, sm, j, n_log2, tw, twn_log2);
+    bool bad = false;
+    if (live) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            bad |= !finite2(v[r]);
+            rowp[j + q * r] = v[r];
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+template <typename R, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_rows_r2c_reg(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, long long Mp,
+               int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
+               int twn_log2) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2, q = n >> 4;
+    const int ss = seq_stride(n);
+    const int c = threadIdx.x / q, j = threadIdx.x - c * q;
+    const long long row = (long long)blockIdx.x * rpc + c;
+    const bool live = row < nrows;
+    const SeqView<C> sm{small + c * ss};
+    const C* rowp = reinterpret_cast<const C*>(grid) + (live ? row : 0) * n;
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? __ldg(rowp + j + q * s) : C{0, 0};
+    reg_fft<-1>(v, sm, j, n_log2, tw, twn_log2);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+    __syncthreads();
+    if (!live) return;
+    const int sh = twn_log2 - n_log2 - 1;
+    C* h = H + row * Mp;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = j + q * r;
+        const C zk = v[r], znk = sm[(n - k) & (n - 1)];
+        const C xe = cscale(cadd(zk, cconj(znk)), (R)0.5);
+        const C xo = cscale(cmul_mi(csub(zk, cconj(znk))), (R)0.5);
+        h[k] = cadd(xe, cmul(tw[k << sh], xo));
+        if (k == 0) h[n] = csub(xe, xo);   // X[n] = Xe[0] - Xo[0] (both real)
+    }
+}
+
+template <typename R, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_rows_c2r_reg(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, long long Mp,
+               int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
+               int twn_log2, int* status) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n = 1 << n_log2, q = n >> 4;
+    const int ss = seq_stride(n);
+    const int c = threadIdx.x / q, j = threadIdx.x - c * q;
+    const long long row = (long long)blockIdx.x * rpc + c;
+    const bool live = row < nrows;
+    const SeqView<C> sm{small + c * ss};
+    const C* h = H + (live ? row : 0) * Mp;
+    const int sh = twn_log2 - n_log2 - 1;
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int k = j + q * s;
+        const C yk = live ? __ldg(h + k) : C{0, 0};
+        const C ynk = live ? __ldg(h + (n - k)) : C{0, 0};
+        const C wk = tw[k << sh];
+        v[s] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
+    }
+    reg_fft<+1>(v, sm, j, n_log2, tw, twn_log2);
+    bool bad = false;
+    if (live) {
+        C* rowp = reinterpret_cast<C*>(grid) + row * n;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            bad |= !finite2(v[r]);
+            rowp[j + q * r] = v[r];
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+template <typename R, int DIR, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_cols_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
+           const typename CxOf<R>::T* __restrict__ tw, int twn_log2) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n = 1 << g.log2n, q = n >> 4;
+    const int cols = 1 << g.cols_log2;
+    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> g.cols_log2;
+    const int i0 = blockIdx.x << g.cols_log2;
+    const bool live = i0 + c < g.inner_valid;
+    const ColView<C> sm{small, c, g.cols_log2};
+    C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : C{0, 0};
+    reg_fft<DIR>(v, sm, j, g.log2n, tw, twn_log2);
+    if (live) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
+    }
+}
+
+template <typename R, int RAD, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
+                 const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
+                 const __grid_constant__ SymbolParams p) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n = 1 << g.log2n, q = n >> 4;
+    const int cols = 1 << g.cols_log2;
+    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> g.cols_log2;
+    const int i0 = blockIdx.x << g.cols_log2;
+    const bool live = i0 + c < g.inner_valid;
+    const ColView<C> sm{small, c, g.cols_log2};
+    C* base = H + (long long)blockIdx.y * g.ms + i0 + c;
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : C{0, 0};
+    reg_fft<-1>(v, sm, j, g.log2n, tw, twn_log2);
+    int k[3];
+    if (p.ndim == 2) {
+        k[1] = i0 + c;
+        k[2] = 0;
+    } else {
+        k[1] = blockIdx.y;
+        k[2] = i0 + c;
+    }
+    ColSymbol<RAD> cs;
+    col_symbol_init<RAD>(p, k, cs);
+    apply_multiplier<RAD>(v, sm, j, q, p, cs, k[1], k[2]);
+    __syncthreads();
+    reg_fft<+1>(v, sm, j, g.log2n, tw, twn_log2);
+    if (live) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
 int cols_log2_for(int log2n, int elem_bytes, int max_threads) {
@@ -320,11 +534,146 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// rows per CTA of the register kernels: up to 256 threads per CTA
+static int reg_rows_per_cta(int n_log2) {
+    const int q = 1 << (n_log2 - 4);
+    int rpc = 1;
+    while (rpc * 2 * q <= 256) rpc *= 2;
+    return rpc;
+}
+
+// Threads per CTA of the register column kernels (512 or 1024; the
+// environment variable STENCILFFT_COL_THREADS overrides the default of 1024).
+static int col_threads_cap() {
+    static int cap = [] {
+        const char* e = std::getenv("STENCILFFT_COL_THREADS");
+        const int v = e ? std::atoi(e) : 1024;
+        return v == 512 ? 512 : 1024;
+    }();
+    return cap;
+}
+
+template <typename R, int RAD, int MAXT>
+static cudaError_t launch_fused_1d_reg_t(R* grid, int n_log2, int nrows, const void* tw,
+                                         int twn_log2, const SymbolParams& p, int* status,
+                                         cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = reg_rows_per_cta(n_log2);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    const int threads = rpc * (n >> 4);
+    cudaError_t err = set_smem(k_fused_1d_reg<R, RAD, MAXT>, smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = (nrows + rpc - 1) / rpc;
+    k_fused_1d_reg<R, RAD, MAXT><<<blocks, threads, smem, s>>>(
+        grid, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2, p, status);
+    return cudaGetLastError();
+}
+
+template <typename R, int RAD>
+static cudaError_t launch_fused_1d_reg_r(R* grid, int n_log2, int nrows, const void* tw,
+                                         int twn_log2, const SymbolParams& p, int* status,
+                                         cudaStream_t s) {
+    if ((1 << (n_log2 - 4)) <= 256)
+        return launch_fused_1d_reg_t<R, RAD, 256>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+    return launch_fused_1d_reg_t<R, RAD, MaxT<R>::v>(grid, n_log2, nrows, tw, twn_log2, p, status,
+                                                     s);
+}
+
+template <typename R, int MAXT>
+static cudaError_t launch_rows_r2c_reg(const R* grid, void* H, long long Mp, int n_log2,
+                                       int nrows, const void* tw, int twn_log2, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = reg_rows_per_cta(n_log2);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    cudaError_t err = set_smem(k_rows_r2c_reg<R, MAXT>, smem);
+    if (err != cudaSuccess) return err;
+    k_rows_r2c_reg<R, MAXT><<<(nrows + rpc - 1) / rpc, rpc * (n >> 4), smem, s>>>(
+        grid, static_cast<C*>(H), Mp, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2);
+    return cudaGetLastError();
+}
+
+template <typename R, int MAXT>
+static cudaError_t launch_rows_c2r_reg(const void* H, R* grid, long long Mp, int n_log2,
+                                       int nrows, const void* tw, int twn_log2, int* status,
+                                       cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << n_log2;
+    const int rpc = reg_rows_per_cta(n_log2);
+    const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
+    cudaError_t err = set_smem(k_rows_c2r_reg<R, MAXT>, smem);
+    if (err != cudaSuccess) return err;
+    k_rows_c2r_reg<R, MAXT><<<(nrows + rpc - 1) / rpc, rpc * (n >> 4), smem, s>>>(
+        static_cast<const C*>(H), grid, Mp, n_log2, nrows, rpc, static_cast<const C*>(tw),
+        twn_log2, status);
+    return cudaGetLastError();
+}
+
+// column count (log2) of the register column kernels for MAXT threads per CTA
+static int reg_cols_log2(int log2n, int elem_bytes, int maxt) {
+    const int q = 1 << (log2n - 4);
+    int cl = 0;
+    while (cl < 4 && (2 << cl) * q <= maxt &&
+           (long long)colview_elems(1 << log2n, 2 << cl) * elem_bytes <= kSmemBudget)
+        ++cl;
+    return cl;
+}
+
+template <typename R, int DIR, int MAXT>
+static cudaError_t launch_cols_reg(void* H, ColGeom g, const void* tw, int twn_log2,
+                                   cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << g.log2n;
+    g.cols_log2 = reg_cols_log2(g.log2n, sizeof(C), MAXT);
+    const int cols = 1 << g.cols_log2;
+    const size_t smem = (size_t)colview_elems(n, cols) * sizeof(C);
+    cudaError_t err = set_smem(k_cols_reg<R, DIR, MAXT>, smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
+    k_cols_reg<R, DIR, MAXT><<<grid, cols * (n >> 4), smem, s>>>(static_cast<C*>(H), g,
+                                                                  static_cast<const C*>(tw),
+                                                                  twn_log2);
+    return cudaGetLastError();
+}
+
+template <typename R, int RAD, int MAXT>
+static cudaError_t launch_cols_fused_reg_t(void* H, ColGeom g, const void* tw, int twn_log2,
+                                           const SymbolParams& p, cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n = 1 << g.log2n;
+    g.cols_log2 = reg_cols_log2(g.log2n, sizeof(C), MAXT);
+    const int cols = 1 << g.cols_log2;
+    const size_t smem = (size_t)colview_elems(n, cols) * sizeof(C);
+    cudaError_t err = set_smem(k_cols_fused_reg<R, RAD, MAXT>, smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, 1);
+    k_cols_fused_reg<R, RAD, MAXT><<<grid, cols * (n >> 4), smem, s>>>(
+        static_cast<C*>(H), g, static_cast<const C*>(tw), twn_log2, p);
+    return cudaGetLastError();
+}
+
+template <typename R, int RAD>
+static cudaError_t launch_cols_fused_reg_r(void* H, const ColGeom& g, const void* tw,
+                                           int twn_log2, const SymbolParams& p, cudaStream_t s) {
+    if (sizeof(R) == 8 || col_threads_cap() == 512)
+        return launch_cols_fused_reg_t<R, RAD, 512>(H, g, tw, twn_log2, p, s);
+    return launch_cols_fused_reg_t<R, RAD, 1024>(H, g, tw, twn_log2, p, s);
+}
+
 template <typename R>
 cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
                             const SymbolParams& p, int* status, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << n_log2;
+    if (n_log2 >= 4 && (n >> 4) <= MaxT<R>::v) {
+        switch (p.r) {
+            case 0: return launch_fused_1d_reg_r<R, 0>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+            case 1: return launch_fused_1d_reg_r<R, 1>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+            case 2: return launch_fused_1d_reg_r<R, 2>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+            default: return launch_fused_1d_reg_r<R, 3>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+        }
+    }
     const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
@@ -341,6 +690,11 @@ cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, in
                             const void* tw, int twn_log2, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << n_log2;
+    if (n_log2 >= 4 && (n >> 4) <= MaxT<R>::v) {
+        if ((n >> 4) <= 256)
+            return launch_rows_r2c_reg<R, 256>(grid, H, Mp, n_log2, nrows, tw, twn_log2, s);
+        return launch_rows_r2c_reg<R, MaxT<R>::v>(grid, H, Mp, n_log2, nrows, tw, twn_log2, s);
+    }
     const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
@@ -357,6 +711,12 @@ cudaError_t launch_rows_c2r(const void* H, R* grid, long long Mp, int n_log2, in
                             const void* tw, int twn_log2, int* status, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << n_log2;
+    if (n_log2 >= 4 && (n >> 4) <= MaxT<R>::v) {
+        if ((n >> 4) <= 256)
+            return launch_rows_c2r_reg<R, 256>(H, grid, Mp, n_log2, nrows, tw, twn_log2, status, s);
+        return launch_rows_c2r_reg<R, MaxT<R>::v>(H, grid, Mp, n_log2, nrows, tw, twn_log2, status,
+                                                  s);
+    }
     const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
@@ -374,6 +734,14 @@ cudaError_t launch_cols(void* H, const ColGeom& g, int dir, const void* tw, int 
     using C = typename CxOf<R>::T;
     const int n = 1 << g.log2n;
     const int cols = 1 << g.cols_log2;
+    if (g.log2n >= 4 && (n >> 4) <= MaxT<R>::v) {
+        const bool small = sizeof(R) == 8 || col_threads_cap() == 512;
+        if (dir < 0)
+            return small ? launch_cols_reg<R, -1, 512>(H, g, tw, twn_log2, s)
+                         : launch_cols_reg<R, -1, 1024>(H, g, tw, twn_log2, s);
+        return small ? launch_cols_reg<R, +1, 512>(H, g, tw, twn_log2, s)
+                     : launch_cols_reg<R, +1, 1024>(H, g, tw, twn_log2, s);
+    }
     const size_t smem = (size_t)cols * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)cols * n, MaxT<R>::v);
     dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
@@ -398,6 +766,14 @@ cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn
     using C = typename CxOf<R>::T;
     const int n = 1 << g.log2n;
     const int cols = 1 << g.cols_log2;
+    if (g.log2n >= 4 && (n >> 4) <= MaxT<R>::v) {
+        switch (p.r) {
+            case 0: return launch_cols_fused_reg_r<R, 0>(H, g, tw, twn_log2, p, s);
+            case 1: return launch_cols_fused_reg_r<R, 1>(H, g, tw, twn_log2, p, s);
+            case 2: return launch_cols_fused_reg_r<R, 2>(H, g, tw, twn_log2, p, s);
+            default: return launch_cols_fused_reg_r<R, 3>(H, g, tw, twn_log2, p, s);
+        }
+    }
     const size_t smem = (size_t)cols * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)cols * n, MaxT<R>::v);
     cudaError_t err = set_smem(k_cols_fused<R>, smem);

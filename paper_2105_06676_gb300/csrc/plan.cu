@@ -133,6 +133,11 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
     sp.delta = (float)(wsum * std::ldexp(1.0, -16)) + 1e-30f;
     sp.use_cut = 1;
     sp.cut = p->precision == STENCIL_FP32 ? 154.0f : 1080.0f;
+    sp.tau2 = -1.0f;
+    if (T > 0) {
+        const double tau = std::exp2(-(double)sp.cut / (double)T) - (double)sp.delta;
+        if (tau > 0) sp.tau2 = (float)(tau * tau * (1.0 - std::ldexp(1.0, -20)));
+    }
     return sp;
 }
 

@@ -34,6 +34,9 @@ struct SymbolParams {
     int use_cut;
     float delta;           // bound on |Lambda - Lambda_fp32|
     float cut;             // skip when T log2(|Lambda_fp32| + delta) < -cut
+    float tau2;            // same test as |Lambda_fp32|^2 < tau2, tau = 2^(-cut/T) - delta
+                           // (with a relative margin for the rounding of the square);
+                           // negative when no element can be skipped
     int len[3];            // axis lengths l_a of the solved box (full length of the halved last axis)
     int tshift[3];         // tables hold exp(2 pi i q / (l_a << tshift)): index scale of this box
     int tmask[3];          // l_a - 1
@@ -145,6 +148,129 @@ __device__ __forceinline__ C spectral_multiplier(const SymbolParams& p, const in
     }
     const double2 v = lambda_pow64(p, k);
     return C{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+}
+
+// Per-column part of Lambda for a pass along axis 0: with k_0 the transform
+// index and k_1.. fixed for the column,
+//   Lambda(k) = sum_{m_0} E_0[m_0 k_0] G[m_0],
+//   G[m_0]    = sum_{m_1..} w[m_0, m_1, ..] prod_{a >= 1} E_a[m_a k_a]      (FP32).
+template <int RAD>
+struct ColSymbol {
+    float2 g[2 * RAD + 1];
+};
+
+template <int RAD>
+__device__ __forceinline__ void col_symbol_init(const SymbolParams& p, const int* k,
+                                                ColSymbol<RAD>& cs) {
+    constexpr int W = 2 * RAD + 1;
+    if (p.ndim == 1) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) cs.g[i] = float2{p.w32[i], 0.f};
+        return;
+    }
+    float2 e1[W], e2[W];
+#pragma unroll
+    for (int m = -RAD; m <= RAD; ++m)
+        e1[m + RAD] = __ldg(p.E32[1] + (((m * k[1]) & p.tmask[1]) << p.tshift[1]));
+    if (p.ndim == 2) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            float2 acc{0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < W; ++jj) acc = cadd(acc, cscale(e1[jj], p.w32[i * W + jj]));
+            cs.g[i] = acc;
+        }
+        return;
+    }
+#pragma unroll
+    for (int m = -RAD; m <= RAD; ++m)
+        e2[m + RAD] = __ldg(p.E32[2] + (((m * k[2]) & p.tmask[2]) << p.tshift[2]));
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        float2 acc{0.f, 0.f};
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj) {
+            float2 inner{0.f, 0.f};
+#pragma unroll
+            for (int qq = 0; qq < W; ++qq)
+                inner = cadd(inner, cscale(e2[qq], p.w32[(i * W + jj) * W + qq]));
+            acc = cadd(acc, cmul(e1[jj], inner));
+        }
+        cs.g[i] = acc;
+    }
+}
+
+// FP32 value of Lambda at k_0 for the column described by cs; E[-q] is
+// conj(E[q]) and E[0] = 1, so RAD table loads suffice.
+template <int RAD>
+__device__ __forceinline__ float2 col_lambda32(const SymbolParams& p, const ColSymbol<RAD>& cs,
+                                               int k0) {
+    float2 l = cs.g[RAD];
+#pragma unroll
+    for (int m = 1; m <= RAD; ++m) {
+        const float2 e = __ldg(p.E32[0] + (((m * k0) & p.tmask[0]) << p.tshift[0]));
+        l = cadd(l, cmul(e, cs.g[RAD + m]));
+        l = cadd(l, cmul(cconj(e), cs.g[RAD - m]));
+    }
+    return l;
+}
+
+// Multiply the survivors (bits of mask) of a thread's 16 elements, parked in
+// shared memory at sm[spad(j + q r)], by V = Lambda^T / N in FP64 (kept out of
+// line so the caller's registers are not held across it).
+template <typename C, typename View>
+__device__ __noinline__ void multiply_survivors(View sm, int j, int q, unsigned mask,
+                                                const SymbolParams& p, int k1, int k2) {
+    using R = decltype(C{}.x);
+    while (mask) {
+        const int r = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int k[3] = {j + q * r, k1, k2};
+        const double2 v = lambda_pow64(p, k);
+        const C V{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+        C& e = sm[j + q * r];
+        e = cmul(e, V);
+    }
+}
+
+// x * V[k] for a single frequency k (out of line; used for the one Nyquist
+// element of a real axis).
+template <typename C>
+__device__ __noinline__ C multiply_single(C x, const SymbolParams& p, int k0, int k1, int k2) {
+    const int k[3] = {k0, k1, k2};
+    return cmul(x, spectral_multiplier<C>(p, k));
+}
+
+// v[r] <- V[k] v[r] for the thread's elements k_0 = j + q r of one column whose
+// other frequencies are (k1, k2) and whose FP32 factorisation is cs. Elements
+// whose FP32 bound shows |V| below half the smallest subnormal become 0; the
+// rest get the FP64 multiplier. sm (this sequence's shared buffer) is used as
+// scratch at the thread's own positions; the caller must place a barrier
+// between this and the next use of sm by other threads.
+template <int RAD, typename C, typename View>
+__device__ __forceinline__ void apply_multiplier(C* v, const View& sm, int j, int q,
+                                                 const SymbolParams& p, const ColSymbol<RAD>& cs,
+                                                 int k1, int k2) {
+    using R = decltype(C{}.x);
+    if (p.T == 0) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], (R)p.scale);
+        return;
+    }
+    unsigned mask = 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const float2 l = col_lambda32<RAD>(p, cs, j + q * r);
+        if (l.x * l.x + l.y * l.y < p.tau2) v[r] = C{(R)0, (R)0};
+        else mask |= 1u << r;
+    }
+    if (mask) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+        multiply_survivors<C, View>(sm, j, q, mask, p, k1, k2);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = mask >> r & 1 ? sm[j + q * r] : C{(R)0, (R)0};
+    }
 }
 
 }  // namespace sfft
