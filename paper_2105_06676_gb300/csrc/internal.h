@@ -47,12 +47,17 @@ cudaError_t launch_cols(void* H, const ColGeom& g, int dir, const void* tw, int 
                         cudaStream_t s);
 template <typename R>
 cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn_log2,
-                              const SymbolParams& p, cudaStream_t s);
+                              const SymbolSet& p, cudaStream_t s);
 template <typename R>
 cudaError_t launch_twiddles(void* tw, int twn_log2, cudaStream_t s);
+template <typename R>
+cudaError_t launch_vtable(void* V, const SymbolParams& p, long long Mp, cudaStream_t s);
 cudaError_t launch_axis_table(double2* E64, float2* E32, int len, cudaStream_t s);
 cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_half,
                                 long long total, cudaStream_t s);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
+cudaError_t smem_optin(const void* kernel, size_t bytes);
 
 // Number of columns per CTA the column kernels use for a transform of 2^log2n.
 int cols_log2_for(int log2n, int elem_bytes, int max_threads);

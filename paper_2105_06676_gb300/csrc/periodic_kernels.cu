@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "fft_reg.cuh"
 #include "internal.h"
@@ -215,12 +217,13 @@ template <typename R>
 __global__ void __launch_bounds__(MaxT<R>::v)
 k_cols_fused(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
              const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
-             const __grid_constant__ SymbolParams p) {
+             const __grid_constant__ SymbolSet ps) {
+    const SymbolParams& p = ps.p[ps.orient[blockIdx.z]];
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int i0 = blockIdx.x << g.cols_log2;
-    C* base = H + (long long)blockIdx.y * g.ms + i0;
+    C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0;
     load_cols(sm, base, g, i0);
     __syncthreads();
     const int cols = min(1 << g.cols_log2, g.inner_valid - i0);
@@ -237,7 +240,11 @@ k_cols_fused(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeo
             k[1] = blockIdx.y;
             k[2] = i0 + c;
         }
-        const C v = spectral_multiplier<C>(p, k);
+        const C* vt = static_cast<const C*>(ps.vtab[ps.orient[blockIdx.z]]);
+        const C v = vt ? (i0 + c < g.inner_valid
+                              ? vt[(long long)blockIdx.y * g.ms + (long long)j * g.S + i0 + c]
+                              : C{0, 0})
+                       : spectral_multiplier<C>(p, k);
         C* q = sm + c * ss + spad(j);
         *q = cmul(*q, v);
     }
@@ -282,6 +289,31 @@ __global__ void k_symbol_table(double2* out, const __grid_constant__ SymbolParam
             rest /= p.len[a];
         }
         out[e] = lambda_pow64(p, k);
+    }
+}
+
+// V[k] = Lambda[k]^T / N at pass precision for one box shape, laid out like
+// one item's half spectrum: ((k_0 * l_1 + k_1) * Mp + k_last) (d = 3) or
+// (k_0 * Mp + k_1) (d = 2).
+template <typename R>
+__global__ void k_vtable(typename CxOf<R>::T* __restrict__ V, const __grid_constant__ SymbolParams p,
+                         int nhalf, long long Mp, long long total) {
+    using C = typename CxOf<R>::T;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int k[3] = {0, 0, 0};
+        long long rest = e;
+        const int last = (int)(rest % nhalf);
+        rest /= nhalf;
+        if (p.ndim == 2) {
+            k[0] = (int)rest;
+            k[1] = last;
+        } else {
+            k[1] = (int)(rest % p.len[1]);
+            k[0] = (int)(rest / p.len[1]);
+            k[2] = last;
+        }
+        V[rest * Mp + last] = spectral_multiplier<C>(p, k);
     }
 }
 
@@ -462,7 +494,8 @@ template <typename R, int RAD, int MAXT>
 __global__ void __launch_bounds__(MAXT)
 k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
                  const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
-                 const __grid_constant__ SymbolParams p) {
+                 const __grid_constant__ SymbolSet ps) {
+    const SymbolParams& p = ps.p[ps.orient[blockIdx.z]];
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
@@ -472,7 +505,7 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
     const int i0 = blockIdx.x << g.cols_log2;
     const bool live = i0 + c < g.inner_valid;
     const ColView<C> sm{small, c, g.cols_log2};
-    C* base = H + (long long)blockIdx.y * g.ms + i0 + c;
+    C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
     C v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : C{0, 0};
@@ -485,9 +518,19 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
         k[1] = blockIdx.y;
         k[2] = i0 + c;
     }
-    ColSymbol<RAD> cs;
-    col_symbol_init<RAD>(p, k, cs);
-    apply_multiplier<RAD>(v, sm, j, q, p, cs, k[1], k[2]);
+    const C* vt = static_cast<const C*>(ps.vtab[ps.orient[blockIdx.z]]);
+    if (vt) {
+        // multipliers shared by every solve of this shape and T, built once per run
+        const C* vbase = vt + (long long)blockIdx.y * g.ms + i0 + c;
+        if (live) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], __ldg(vbase + (long long)(j + q * r) * g.S));
+        }
+    } else {
+        ColSymbol<RAD> cs;
+        col_symbol_init<RAD>(p, k, cs);
+        apply_multiplier<RAD>(v, sm, j, q, p, cs, k[1], k[2]);
+    }
     __syncthreads();
     reg_fft<+1>(v, sm, j, g.log2n, tw, twn_log2);
     if (live) {
@@ -499,6 +542,20 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
+cudaError_t smem_optin(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{kernel, dev}];
+    if (bytes <= have) return cudaSuccess;
+    cudaError_t err =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err == cudaSuccess) have = bytes;
+    return err;
+}
+
 int cols_log2_for(int log2n, int elem_bytes, int max_threads) {
     const int n = 1 << log2n;
     int cl = 0;
@@ -528,10 +585,12 @@ static int threads_for(long long elems, int max_threads) {
     return (int)t;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device); later
+// launches (including those recorded into a CUDA graph) make no runtime call.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return smem_optin(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 // rows per CTA of the register kernels: up to 256 threads per CTA
@@ -639,7 +698,7 @@ static cudaError_t launch_cols_reg(void* H, ColGeom g, const void* tw, int twn_l
 
 template <typename R, int RAD, int MAXT>
 static cudaError_t launch_cols_fused_reg_t(void* H, ColGeom g, const void* tw, int twn_log2,
-                                           const SymbolParams& p, cudaStream_t s) {
+                                           const SymbolSet& p, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << g.log2n;
     g.cols_log2 = reg_cols_log2(g.log2n, sizeof(C), MAXT);
@@ -647,7 +706,7 @@ static cudaError_t launch_cols_fused_reg_t(void* H, ColGeom g, const void* tw, i
     const size_t smem = (size_t)colview_elems(n, cols) * sizeof(C);
     cudaError_t err = set_smem(k_cols_fused_reg<R, RAD, MAXT>, smem);
     if (err != cudaSuccess) return err;
-    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, 1);
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
     k_cols_fused_reg<R, RAD, MAXT><<<grid, cols * (n >> 4), smem, s>>>(
         static_cast<C*>(H), g, static_cast<const C*>(tw), twn_log2, p);
     return cudaGetLastError();
@@ -655,7 +714,7 @@ static cudaError_t launch_cols_fused_reg_t(void* H, ColGeom g, const void* tw, i
 
 template <typename R, int RAD>
 static cudaError_t launch_cols_fused_reg_r(void* H, const ColGeom& g, const void* tw,
-                                           int twn_log2, const SymbolParams& p, cudaStream_t s) {
+                                           int twn_log2, const SymbolSet& p, cudaStream_t s) {
     if (sizeof(R) == 8 || col_threads_cap() == 512)
         return launch_cols_fused_reg_t<R, RAD, 512>(H, g, tw, twn_log2, p, s);
     return launch_cols_fused_reg_t<R, RAD, 1024>(H, g, tw, twn_log2, p, s);
@@ -762,12 +821,12 @@ cudaError_t launch_cols(void* H, const ColGeom& g, int dir, const void* tw, int 
 
 template <typename R>
 cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn_log2,
-                              const SymbolParams& p, cudaStream_t s) {
+                              const SymbolSet& p, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << g.log2n;
     const int cols = 1 << g.cols_log2;
     if (g.log2n >= 4 && (n >> 4) <= MaxT<R>::v) {
-        switch (p.r) {
+        switch (p.p[0].r) {
             case 0: return launch_cols_fused_reg_r<R, 0>(H, g, tw, twn_log2, p, s);
             case 1: return launch_cols_fused_reg_r<R, 1>(H, g, tw, twn_log2, p, s);
             case 2: return launch_cols_fused_reg_r<R, 2>(H, g, tw, twn_log2, p, s);
@@ -778,9 +837,21 @@ cudaError_t launch_cols_fused(void* H, const ColGeom& g, const void* tw, int twn
     const int threads = threads_for((long long)cols * n, MaxT<R>::v);
     cudaError_t err = set_smem(k_cols_fused<R>, smem);
     if (err != cudaSuccess) return err;
-    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, 1);
+    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
     k_cols_fused<R><<<grid, threads, smem, s>>>(static_cast<C*>(H), g, static_cast<const C*>(tw),
                                                  twn_log2, p);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_vtable(void* V, const SymbolParams& p, long long Mp, cudaStream_t s) {
+    const int nhalf = p.len[p.ndim - 1] / 2 + 1;
+    long long total = nhalf;
+    for (int a = 0; a < p.ndim - 1; ++a) total *= p.len[a];
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_vtable<R><<<(int)blocks, 256, 0, s>>>(static_cast<typename CxOf<R>::T*>(V), p, nhalf, Mp,
+                                            total);
     return cudaGetLastError();
 }
 
@@ -820,8 +891,9 @@ cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_h
     template cudaError_t launch_cols<R>(void*, const ColGeom&, int, const void*, int,              \
                                         cudaStream_t);                                             \
     template cudaError_t launch_cols_fused<R>(void*, const ColGeom&, const void*, int,             \
-                                              const SymbolParams&, cudaStream_t);                  \
-    template cudaError_t launch_twiddles<R>(void*, int, cudaStream_t);
+                                              const SymbolSet&, cudaStream_t);                  \
+    template cudaError_t launch_twiddles<R>(void*, int, cudaStream_t);                            \
+    template cudaError_t launch_vtable<R>(void*, const SymbolParams&, long long, cudaStream_t);
 
 SFFT_INSTANTIATE(float)
 SFFT_INSTANTIATE(double)

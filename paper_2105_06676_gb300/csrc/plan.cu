@@ -102,32 +102,50 @@ static bool symmetric_weights(const double* w, int ndim, int r) {
     return true;
 }
 
-// Symbol parameters for a periodic solve of a box of shape len[0..ndim-1]
-// with the plan's weights (optionally transposed weights for strips).
+// Symbol parameters for a periodic solve of a box of shape len[0..ndim-1].
+// perm (optional) maps box axis a to grid axis perm[a]: the box then holds a
+// transposed region of the grid, and Lambda uses the correspondingly permuted
+// weights and the grid axis' tables.
 SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
-                                const double2* const* E64, const float2* const* E32) {
+                                const double2* const* E64, const float2* const* E32,
+                                const int* perm) {
     SymbolParams sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.ndim = p->ndim;
     sp.r = p->radius;
     sp.T = (long long)T;
+    int pm[3] = {0, 1, 2};
+    if (perm)
+        for (int a = 0; a < p->ndim; ++a) pm[a] = perm[a];
     double N = 1.0;
     for (int a = 0; a < p->ndim; ++a) {
+        const int ga = pm[a];
         sp.len[a] = (int)len[a];
-        sp.tshift[a] = ilog2_exact(p->dims[a]) - ilog2_exact(len[a]);
+        sp.tshift[a] = ilog2_exact(p->dims[ga]) - ilog2_exact(len[a]);
         sp.tmask[a] = (int)(len[a] - 1);
         N *= (double)len[a];
-        sp.E64[a] = E64[a];
-        sp.E32[a] = E32[a];
+        sp.E64[a] = E64[ga];
+        sp.E32[a] = E32[ga];
+    }
+    // permuted weights: box offset m' has grid offset m with m[pm[a]] = m'[a]
+    const int W = 2 * p->radius + 1;
+    double wsum = 0.0;
+    for (int i = 0; i < p->nweights; ++i) {
+        int rest = i, digits[3] = {0, 0, 0};
+        for (int a = p->ndim - 1; a >= 0; --a) {
+            digits[a] = rest % W;   // box-axis digit m'_a + r
+            rest /= W;
+        }
+        int gd[3] = {0, 0, 0};
+        for (int a = 0; a < p->ndim; ++a) gd[pm[a]] = digits[a];
+        int gi = 0;
+        for (int a = 0; a < p->ndim; ++a) gi = gi * W + gd[a];
+        sp.w[i] = p->weights[gi];
+        sp.w32[i] = (float)p->weights[gi];
+        wsum += std::fabs(p->weights[gi]);
     }
     sp.scale = 1.0 / N;
     sp.real_symbol = p->real_symbol ? 1 : 0;
-    double wsum = 0.0;
-    for (int i = 0; i < p->nweights; ++i) {
-        sp.w[i] = p->weights[i];
-        sp.w32[i] = (float)p->weights[i];
-        wsum += std::fabs(p->weights[i]);
-    }
     // |Lambda - Lambda_fp32| <= sum|w| * 2^-16: a generous bound on the error of
     // at most 343 products of <= 3 rounded table entries and a rounded weight.
     sp.delta = (float)(wsum * std::ldexp(1.0, -16)) + 1e-30f;
@@ -188,40 +206,55 @@ size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision) {
         if (err != cudaSuccess) return err; \
     } while (0)
 
+// Periodic solve of `items` boxes of shape len stacked contiguously in S (in
+// place), with their half spectra stacked in H (row stride Mp). Item i is a
+// grid region in orientation perms[orient[i]] (box axis a = grid axis
+// perms[..][a]); all items share one launch per pass.
 template <typename R>
-cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
-                           void* H, long long Mp, const void* tw, int twn_log2,
-                           const double2* const* E64, const float2* const* E32, int* status,
-                           cudaStream_t s) {
+cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items, int64_t T,
+                          void* H, long long Mp, const int* orient, const int (*perms)[3],
+                          int norient, const void* tw, int twn_log2, const double2* const* E64,
+                          const float2* const* E32, int* status, cudaStream_t s,
+                          const void* const* vtabs) {
     const int d = p->ndim;
-    const SymbolParams sp = make_symbol_params(p, len, T, E64, E32);
+    if (items < 1 || items > kMaxItems || norient < 1 || norient > kMaxOrient)
+        return cudaErrorInvalidValue;
+    SymbolSet ss;
+    std::memset(&ss, 0, sizeof(ss));
+    for (int o = 0; o < norient; ++o)
+        ss.p[o] = make_symbol_params(p, len, T, E64, E32, perms ? perms[o] : nullptr);
+    for (int i = 0; i < items; ++i) ss.orient[i] = orient ? orient[i] : 0;
+    for (int o = 0; o < norient; ++o) ss.vtab[o] = vtabs ? vtabs[o] : nullptr;
     const int maxt = sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64;
     const int celem = 2 * sizeof(R);
     const int n_log2 = ilog2_exact(len[d - 1]) - 1;
     const int n = 1 << n_log2;
     cudaError_t err;
     if (d == 1) {
-        PROF_LAUNCH(PASS_FUSED_1D, launch_fused_1d<R>(grid, n_log2, 1, tw, twn_log2, sp, status, s));
+        // every item of a 1-D batch has the one orientation
+        PROF_LAUNCH(PASS_FUSED_1D,
+                    launch_fused_1d<R>(S, n_log2, items, tw, twn_log2, ss.p[0], status, s));
         return cudaSuccess;
     }
-    const int64_t rows = d == 2 ? len[0] : len[0] * len[1];
-    PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_r2c<R>(grid, H, Mp, n_log2, (int)rows, tw, twn_log2, s));
+    const int64_t rows_item = d == 2 ? len[0] : len[0] * len[1];
+    const int64_t rows = rows_item * items;
+    PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_r2c<R>(S, H, Mp, n_log2, (int)rows, tw, twn_log2, s));
     if (d == 2) {
         ColGeom g;
         g.log2n = ilog2_exact(len[0]);
         g.S = Mp;
-        g.outer = 1;
-        g.os = 0;
+        g.outer = items;
+        g.os = len[0] * Mp;
         g.mid = 1;
         g.ms = 0;
         g.inner_valid = n + 1;
         g.cols_log2 = cols_log2_for(g.log2n, celem, maxt);
-        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, sp, s));
+        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, ss, s));
     } else {
         ColGeom g1;
         g1.log2n = ilog2_exact(len[1]);
         g1.S = Mp;
-        g1.outer = (int)len[0];
+        g1.outer = (int)(len[0] * items);
         g1.os = len[1] * Mp;
         g1.mid = 1;
         g1.ms = 0;
@@ -231,28 +264,40 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
         ColGeom g0;
         g0.log2n = ilog2_exact(len[0]);
         g0.S = len[1] * Mp;
-        g0.outer = 1;
-        g0.os = 0;
+        g0.outer = items;
+        g0.os = len[0] * len[1] * Mp;
         g0.mid = (int)len[1];
         g0.ms = Mp;
         g0.inner_valid = n + 1;
         g0.cols_log2 = cols_log2_for(g0.log2n, celem, maxt);
-        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, sp, s));
+        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, ss, s));
         PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
     }
     PROF_LAUNCH(PASS_ROWS_C2R,
-                launch_rows_c2r<R>(H, grid, Mp, n_log2, (int)rows, tw, twn_log2, status, s));
+                launch_rows_c2r<R>(H, S, Mp, n_log2, (int)rows, tw, twn_log2, status, s));
     return cudaSuccess;
 }
 
-template cudaError_t periodic_solve<float>(stencil_plan_s*, float*, const int64_t*, int64_t,
-                                           void*, long long, const void*, int,
-                                           const double2* const*, const float2* const*, int*,
-                                           cudaStream_t);
-template cudaError_t periodic_solve<double>(stencil_plan_s*, double*, const int64_t*,
-                                            int64_t, void*, long long, const void*, int,
-                                            const double2* const*, const float2* const*, int*,
-                                            cudaStream_t);
+template <typename R>
+cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
+                           void* H, long long Mp, const void* tw, int twn_log2,
+                           const double2* const* E64, const float2* const* E32, int* status,
+                           cudaStream_t s) {
+    return batched_solve<R>(p, grid, len, 1, T, H, Mp, nullptr, nullptr, 1, tw, twn_log2, E64, E32,
+                            status, s, nullptr);
+}
+
+#define SFFT_SOLVE_INST(R)                                                                         \
+    template cudaError_t periodic_solve<R>(stencil_plan_s*, R*, const int64_t*, int64_t, void*,    \
+                                           long long, const void*, int, const double2* const*,     \
+                                           const float2* const*, int*, cudaStream_t);              \
+    template cudaError_t batched_solve<R>(stencil_plan_s*, R*, const int64_t*, int, int64_t,       \
+                                          void*, long long, const int*, const int (*)[3], int,     \
+                                          const void*, int, const double2* const*,                 \
+                                          const float2* const*, int*, cudaStream_t,                \
+                                          const void* const*);
+SFFT_SOLVE_INST(float)
+SFFT_SOLVE_INST(double)
 
 }  // namespace sfft
 
@@ -404,7 +449,7 @@ int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int6
 
 int stencil_symbol_power(stencil_plan_t p, int64_t T, void* out, void* stream) {
     if (!p || !out || T < 0) return STENCIL_EINVAL;
-    const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32);
+    const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
     const int nlast_half = (int)(p->dims[p->ndim - 1] / 2 + 1);
     long long total = nlast_half;
     for (int a = 0; a < p->ndim - 1; ++a) total *= p->dims[a];
@@ -445,7 +490,7 @@ extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
 
 static const char* kPassNames[PASS_KINDS] = {
     "rows_r2c", "cols_fwd", "cols_fused", "cols_inv", "rows_c2r", "fused_1d",
-    "strip_r2c", "strip_cols", "strip_c2r", "base_loop", "copy"};
+    "strip_r2c", "strip_cols", "strip_c2r", "base_loop", "copy", "vtable"};
 
 extern "C" int stencil_profile_enable(stencil_plan_t p, int enable) {
     if (!p) return STENCIL_EINVAL;

@@ -23,7 +23,8 @@ enum PassKind {
     PASS_STRIP_C2R = 8,
     PASS_BASE_LOOP = 9,
     PASS_COPY = 10,
-    PASS_KINDS = 11
+    PASS_VTABLE = 11,
+    PASS_KINDS = 12
 };
 
 // Optional CUDA-event bracketing of every kernel launch of a run, on the
@@ -78,8 +79,15 @@ namespace sfft {
 int ilog2_exact(int64_t v);
 int64_t max_axis(int ndim, int precision, int axis);
 SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
-                                const double2* const* E64, const float2* const* E32);
+                                const double2* const* E64, const float2* const* E32,
+                                const int* perm);
 size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision);
+template <typename R>
+cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items, int64_t T,
+                          void* H, long long Mp, const int* orient, const int (*perms)[3],
+                          int norient, const void* tw, int twn_log2, const double2* const* E64,
+                          const float2* const* E32, int* status, cudaStream_t s,
+                          const void* const* vtabs);
 template <typename R>
 cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
                            void* H, long long Mp, const void* tw, int twn_log2,

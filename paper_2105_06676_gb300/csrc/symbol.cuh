@@ -46,6 +46,19 @@ struct SymbolParams {
     float w32[kMaxWeights];
 };
 
+// Symbol parameters for a batch of boxes solved by one launch: up to
+// kMaxOrient orientations (box axes mapped to grid axes by a permutation) and
+// the orientation of each batch item.
+constexpr int kMaxOrient = 3;
+constexpr int kMaxItems = 8;
+struct SymbolSet {
+    SymbolParams p[kMaxOrient];
+    int orient[kMaxItems];
+    // optional precomputed multipliers V = Lambda^T / N per orientation, laid
+    // out like one item's half spectrum (null: evaluate on the fly)
+    const void* vtab[kMaxOrient];
+};
+
 // sum_m w[m] prod_a E_a[(m_a k_a) mod l_a], separably; k[a] in [0, l_a).
 // RAD is the stencil radius as a compile-time constant so the phase factors
 // stay in registers.

@@ -117,3 +117,32 @@ def test_box9_8192_full_size_invariants():
     # distribution, so check the mass against a shorter run: more steps, less mass
     shorter = run_gpu(a0, wk.weights, wk.T // 2, "fp32")
     assert got.sum() <= shorter.sum() + 1e-3 * a0.size * 2e-4
+
+
+@pytest.mark.parametrize("dims,r,T", [((256, 256), 1, 100), ((64,), 2, 40), ((32, 32, 32), 1, 12)])
+def test_graph_replay_matches_eager_run(dims, r, T):
+    # the first run for a T executes eagerly; later runs replay a captured CUDA
+    # graph (per grid buffer). Every run must give the same bits.
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(len(dims), r, 5)
+    a0 = torch.tensor(wl.grid_uniform(dims, 6), dtype=torch.float32, device="cuda")
+    plan = StencilPlan(dims, w, "dirichlet", "fp32")
+    g = a0.clone()
+    plan.run(g, T)
+    first = g.clone()
+    for _ in range(3):
+        g.copy_(a0)
+        plan.run(g, T)
+        torch.cuda.synchronize()
+        assert torch.equal(g, first)
+    other = a0.clone()                        # a second buffer: a second graph
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.run(other, T, stream=side)
+    side.synchronize()
+    assert torch.equal(other, first)
+    assert plan.status() == 0
+    plan.close()
+    ref = oracle.stencil_loop(a0.double().cpu().numpy(), w, T, "dirichlet")
+    assert err_rel(first.double().cpu().numpy(), ref, a0.cpu().numpy()) <= 2e-4

@@ -45,10 +45,10 @@ def decode(v):
             i += 5
             strips = []
             for _ in range(n):
-                f = v[i:i + 13]
-                i += 13
-                strips.append(dict(bdims=f[0:3], off=f[3:6], valid=f[6:9], lo=f[9], hi=f[10],
-                                   face_axis=f[11], face_side=f[12]))
+                f = v[i:i + 16]
+                i += 16
+                strips.append(dict(bdims=f[0:3], off=f[3:6], valid=f[6:9], perm=f[9:12],
+                                   lo=f[12], hi=f[13], face_axis=f[14], face_side=f[15]))
             ops.append(("solve", step, Tk, level, strips))
         elif kind == 2:
             ops.append(("scatter", v[i + 1]))
@@ -67,6 +67,15 @@ def decode(v):
     return ops
 
 
+def region_slices(s, nd):
+    """Grid slices of a strip: grid axis perm[a] spans valid[a] cells from off."""
+    sl = [None] * nd
+    for a in range(nd):
+        ga = s["perm"][a]
+        sl[ga] = slice(s["off"][ga], s["off"][ga] + s["valid"][a])
+    return tuple(sl)
+
+
 def emulate(a0, w, T, ops):
     dims = a0.shape
     nd = a0.ndim
@@ -82,18 +91,23 @@ def emulate(a0, w, T, ops):
             _, step, Tk, level, strips = op
             out = []
             for s in strips:
+                perm = s["perm"][:nd]
                 bd = tuple(s["bdims"][:nd])
                 S = np.zeros(bd)
-                sl_box = tuple(slice(0, s["valid"][a]) for a in range(nd))
-                sl_grid = tuple(slice(s["off"][a], s["off"][a] + s["valid"][a]) for a in range(nd))
-                S[sl_box] = X[sl_grid]
-                out.append(oracle.stencil_fft_periodic(S, w, Tk))
+                # box axis a is grid axis perm[a]: the box holds the region transposed
+                region = X[region_slices(s, nd)]
+                valid = tuple(slice(0, s["valid"][a]) for a in range(nd))
+                S[valid] = np.transpose(region, perm)
+                out.append(oracle.stencil_fft_periodic(S, np.transpose(w, perm), Tk))
             stash[step] = (strips, out)
         elif op[0] == "scatter":
             strips, out = stash.pop(op[1])
             for s, S in zip(strips, out):
-                sl_box = tuple(slice(0, s["valid"][a]) for a in range(nd))
-                sl_grid = tuple(slice(s["off"][a], s["off"][a] + s["valid"][a]) for a in range(nd))
+                perm = s["perm"][:nd]
+                inv = np.argsort(perm)
+                valid = tuple(slice(0, s["valid"][a]) for a in range(nd))
+                back = np.transpose(S[valid], inv)
+                sl_grid = region_slices(s, nd)
                 m = (dist[sl_grid] > s["lo"]) & (dist[sl_grid] <= s["hi"])
                 fa = s["face_axis"]
                 if fa >= 0:
@@ -101,7 +115,7 @@ def emulate(a0, w, T, ops):
                     df = g + 1 if s["face_side"] == 0 else dims[fa] - g
                     m &= df <= s["hi"]
                 sub = X[sl_grid]
-                sub[m] = S[sl_box][m]
+                sub[m] = back[m]
         else:
             _, Tb, tiles = op
             h = r * Tb
@@ -150,9 +164,14 @@ def test_schedule_structure(lib):
     # T = 4096 halves down to 16 < 32: 256 leaves, 255 internal nodes x 2 solves
     assert len(bases) == 256 and len(solves) == 510
     assert all(o[1] == 16 for o in bases)
-    # the top two levels are whole-grid solves, deeper ones four face strips
+    # the top two levels are whole-grid solves, deeper ones four face strips,
+    # the vertical two gathered transposed (face-normal axis first)
     assert all(len(o[4]) == 1 for o in solves if o[3] <= 1)
     assert all(len(o[4]) == 4 for o in solves if o[3] >= 2)
+    for o in solves:
+        if o[3] >= 2:
+            assert [s["perm"][:2] for s in o[4]] == [[0, 1], [0, 1], [1, 0], [1, 0]]
+            assert len({tuple(s["bdims"]) for s in o[4]}) == 1
     # every scatter follows its solve
     seen = set()
     for o in ops:
