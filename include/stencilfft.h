@@ -186,6 +186,57 @@ int stencil_periodic_run_noalloc(int ndim, const int64_t* dims, int radius,
 /* Size in bytes of the fixed scratch array used by stencil_periodic_run_noalloc. */
 size_t stencil_noalloc_scratch_bytes(void);
 
+/* ------------------------------------------------------------------------
+ * Serving: a persistent request loop with continuous batching (the paper has
+ * no serving layer; this is the system around its solver).
+ *
+ * A server owns a worker thread and max_slots non-blocking CUDA streams on the
+ * current device. Requests of any dimension, size, T, boundary, radius and
+ * weights are admitted in arrival order whenever a slot is free and the device
+ * memory of the plan they need fits hbm_budget_bytes (plans -- twiddles,
+ * symbol tables, workspaces -- are pooled by shape and reused; the grids are
+ * the caller's and are not counted). Requests admitted while others run
+ * overlap on the device. Small periodic requests of one shape are batched
+ * into one launch per pass, each with its own Lambda^T table; a request's
+ * result is the same alone or batched.
+ * ------------------------------------------------------------------------ */
+typedef struct stencil_server_s* stencil_server_t;
+
+typedef struct {
+    int ndim;            /* 1..3 */
+    int64_t dims[3];     /* first ndim entries used */
+    int radius;          /* 0..3 */
+    const double* weights; /* (2r+1)^ndim, copied at submit */
+    int boundary;        /* STENCIL_PERIODIC or STENCIL_ZERO_DIRICHLET */
+    int precision;       /* STENCIL_FP64 or STENCIL_FP32 */
+    int64_t T;           /* >= 0 */
+    void* grid;          /* device, 16-byte aligned, solved in place; the caller keeps it
+                            alive and untouched until the ticket completes */
+} stencil_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    int max_in_flight;           /* most slots busy at once */
+    uint64_t batched_launches;   /* launches that carried stacked small requests */
+    uint64_t batched_requests;   /* requests served inside those */
+    size_t bytes_in_use, peak_bytes, budget_bytes;
+} stencil_server_stats_t;
+
+/* Create a server (max_slots 1..64, queue_capacity >= 1, budget > 0). */
+int stencil_server_create(stencil_server_t* out, size_t hbm_budget_bytes, int max_slots,
+                          int queue_capacity);
+/* Queue a request; returns STENCIL_EQUEUEFULL when queue_capacity requests wait,
+ * STENCIL_EINVAL / STENCIL_EUNSUPPORTED for a bad request. Never blocks on the GPU. */
+int stencil_server_submit(stencil_server_t s, const stencil_request* r, uint64_t* ticket);
+/* *done = 1 once the request finished; then returns its status and sets
+ * *latency_s (submit to completion, seconds). */
+int stencil_server_poll(stencil_server_t s, uint64_t ticket, int* done, double* latency_s);
+/* Block until the request finishes (STENCIL_ETIMEOUT after timeout_s seconds). */
+int stencil_server_wait(stencil_server_t s, uint64_t ticket, double timeout_s, double* latency_s);
+int stencil_server_stats(stencil_server_t s, stencil_server_stats_t* out);
+/* Finish every queued request, then release the server and its plans. */
+int stencil_server_destroy(stencil_server_t s);
+
 /* Release a plan and all its device memory (synchronises the device). */
 int stencil_destroy(stencil_plan_t plan);
 

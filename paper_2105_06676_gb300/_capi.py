@@ -48,6 +48,29 @@ SIGNATURES = [
                                             _i64p, _c.c_int64]),
 ]
 
+class StencilRequest(ctypes.Structure):
+    _fields_ = [("ndim", _c.c_int), ("dims", _c.c_int64 * 3), ("radius", _c.c_int),
+                ("weights", _dp), ("boundary", _c.c_int), ("precision", _c.c_int),
+                ("T", _c.c_int64), ("grid", _vp)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _c.c_uint64), ("completed", _c.c_uint64), ("failed", _c.c_uint64),
+                ("max_in_flight", _c.c_int), ("batched_launches", _c.c_uint64),
+                ("batched_requests", _c.c_uint64), ("bytes_in_use", _c.c_size_t),
+                ("peak_bytes", _c.c_size_t), ("budget_bytes", _c.c_size_t)]
+
+
+SIGNATURES += [
+    ("stencil_server_create", _c.c_int, [_c.POINTER(_vp), _c.c_size_t, _c.c_int, _c.c_int]),
+    ("stencil_server_submit", _c.c_int, [_vp, _c.POINTER(StencilRequest), _c.POINTER(_c.c_uint64)]),
+    ("stencil_server_poll", _c.c_int, [_vp, _c.c_uint64, _c.POINTER(_c.c_int),
+                                       _c.POINTER(_c.c_double)]),
+    ("stencil_server_wait", _c.c_int, [_vp, _c.c_uint64, _c.c_double, _c.POINTER(_c.c_double)]),
+    ("stencil_server_stats", _c.c_int, [_vp, _c.POINTER(ServerStats)]),
+    ("stencil_server_destroy", _c.c_int, [_vp]),
+]
+
 _lock = threading.Lock()
 _lib = None
 

@@ -148,3 +148,78 @@ def solve(grid, weights, T: int, boundary: str = "periodic", stream=None):
     finally:
         plan.close()
     return grid
+
+
+class StencilServer:
+    """Continuous-batching request server (stencil_server_*).
+
+    submit() takes a CUDA tensor that the caller keeps alive and untouched until
+    its ticket completes; the solve runs in place on the server's own streams,
+    so every write to the tensor must have completed before submit().
+    """
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 8, queue_capacity: int = 4096):
+        self._h = ctypes.c_void_p()
+        _capi.check(_capi.lib().stencil_server_create(ctypes.byref(self._h), int(hbm_budget_bytes),
+                                                      int(max_slots), int(queue_capacity)),
+                    "stencil_server_create")
+        self._keep = {}
+
+    def submit(self, grid, weights, T: int, boundary: str = "periodic") -> int:
+        """Queue grid (CUDA tensor, solved in place); returns the ticket or raises."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        r = _capi.StencilRequest()
+        r.ndim = grid.dim()
+        for a in range(grid.dim()):
+            r.dims[a] = int(grid.shape[a])
+        r.radius = (w.shape[0] - 1) // 2
+        r.weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.boundary = _BOUNDARY[boundary]
+        r.precision = _capi.STENCIL_FP32 if str(grid.dtype) == "torch.float32" else _capi.STENCIL_FP64
+        r.T = int(T)
+        r.grid = ctypes.c_void_p(grid.data_ptr())
+        t = ctypes.c_uint64()
+        rc = _capi.lib().stencil_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        _capi.check(rc, "stencil_server_submit")
+        self._keep[t.value] = grid
+        return t.value
+
+    def try_submit(self, grid, weights, T: int, boundary: str = "periodic"):
+        """Like submit(), but returns the status code instead of raising (0: queued)."""
+        try:
+            return 0, self.submit(grid, weights, T, boundary)
+        except _capi.StencilError as e:
+            return e.code, None
+
+    def poll(self, ticket: int):
+        """(done, status, latency_s)."""
+        done = ctypes.c_int()
+        lat = ctypes.c_double()
+        rc = _capi.lib().stencil_server_poll(self._h, int(ticket), ctypes.byref(done), ctypes.byref(lat))
+        if done.value:
+            self._keep.pop(ticket, None)
+        return bool(done.value), int(rc), float(lat.value)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        """Block until done; returns (status, latency_s)."""
+        lat = ctypes.c_double()
+        rc = _capi.lib().stencil_server_wait(self._h, int(ticket), float(timeout_s), ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        return int(rc), float(lat.value)
+
+    def stats(self) -> dict:
+        st = _capi.ServerStats()
+        _capi.check(_capi.lib().stencil_server_stats(self._h, ctypes.byref(st)), "stencil_server_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            _capi.lib().stencil_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

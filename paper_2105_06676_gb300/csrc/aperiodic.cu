@@ -471,6 +471,7 @@ struct AperiodicState {
     cudaEvent_t int_fork = nullptr, int_done = nullptr;
     std::map<int64_t, int> runs;             // eager runs so far per T
     std::map<std::pair<int64_t, const void*>, cudaGraphExec_t> graphs;
+    size_t bytes = 0;                        // device memory held (level buffers, tables, scratch)
 };
 
 static int box_Mp(int64_t n, int precision) {
@@ -631,6 +632,7 @@ static cudaError_t ensure_level(AperiodicState* st, int level, size_t sb, size_t
         err = cudaMalloc(&L.S, sb);
         if (err != cudaSuccess) return err;
         L.S_bytes = sb;
+        st->bytes += sb;
     }
     if (L.H_bytes < hb) {
         cudaFree(L.H);
@@ -639,6 +641,7 @@ static cudaError_t ensure_level(AperiodicState* st, int level, size_t sb, size_t
         err = cudaMalloc(&L.H, hb);
         if (err != cudaSuccess) return err;
         L.H_bytes = hb;
+        st->bytes += hb;
     }
     if (!L.stream) {
         err = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
@@ -829,6 +832,7 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
             st->Y = nullptr;
             return err;
         }
+        st->bytes += (size_t)p->n_cells * p->elem;
     }
     if (!st->cap) {
         err = cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking);
@@ -843,11 +847,13 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
         build_rb(p, sc, T, 0, auto_cutoff(p));
         assign_tables(p, sc);
         for (VTable& v : sc.tables) {
-            err = cudaMalloc(&v.buf, periodic_workspace_bytes(p->ndim, v.bdims, p->precision));
+            const size_t vb = periodic_workspace_bytes(p->ndim, v.bdims, p->precision);
+            err = cudaMalloc(&v.buf, vb);
             if (err != cudaSuccess) {
                 v.buf = nullptr;
                 return err;
             }
+            st->bytes += vb;
         }
         for (Step& step : sc.steps) {
             size_t sb = 0, hb = 0;
@@ -863,8 +869,12 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
             if (bs.smem > (size_t)kSmemBudget) return cudaErrorInvalidValue;
             err = cudaMalloc(&bs.tiles, sizeof(BaseTile) * std::max<size_t>(1, tiles.size()));
             if (err != cudaSuccess) return err;
-            err = cudaMemcpy(bs.tiles, tiles.data(), sizeof(BaseTile) * tiles.size(),
-                             cudaMemcpyHostToDevice);
+            // a pageable-memory cudaMemcpy may return before its DMA lands and is
+            // ordered only against the legacy stream; upload on the per-thread
+            // stream and wait, so kernels on any stream see the tiles
+            err = cudaMemcpyAsync(bs.tiles, tiles.data(), sizeof(BaseTile) * tiles.size(),
+                                  cudaMemcpyHostToDevice, cudaStreamPerThread);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(cudaStreamPerThread);
             if (err != cudaSuccess) return err;
             st->base[op.T] = bs;
         }
@@ -1012,12 +1022,13 @@ static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStr
             st->Z = nullptr;
             return err;
         }
+        st->bytes += (size_t)p->n_cells * p->elem;
     }
     // profiled runs: one stream, every launch bracketed by events
     if (p->prof.enabled) return emit<R>(p, st, *sc, grid, T, interior, s, false);
     // the first run for a T goes eagerly (it also sets every kernel attribute)
     int& runs = st->runs[T];
-    if (runs == 0) {
+    if (runs == 0 || !p->use_graphs) {
         ++runs;
         return emit<R>(p, st, *sc, grid, T, interior, s, true);
     }
@@ -1045,6 +1056,14 @@ static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStr
     }
     return cudaGraphLaunch(git->second, s);
 }
+
+void aperiodic_forget_graphs(stencil_plan_s* p) {
+    if (!p || !p->ap) return;
+    for (auto& kv : p->ap->graphs) cudaGraphExecDestroy(kv.second);
+    p->ap->graphs.clear();
+}
+
+size_t aperiodic_bytes(const stencil_plan_s* p) { return p && p->ap ? p->ap->bytes : 0; }
 
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s) {
     cudaError_t err = p->precision == STENCIL_FP32

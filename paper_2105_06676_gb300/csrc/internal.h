@@ -35,7 +35,8 @@ struct ColGeom {
 // Launchers (templated on the real type; instantiated for float and double).
 template <typename R>
 cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
-                            const SymbolParams& p, int* status, cudaStream_t s);
+                            const SymbolParams& p, int* status, cudaStream_t s,
+                            const RowTables* rtab = nullptr);
 template <typename R>
 cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, int nrows,
                             const void* tw, int twn_log2, cudaStream_t s);

@@ -240,7 +240,8 @@ k_cols_fused(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeo
             k[1] = blockIdx.y;
             k[2] = i0 + c;
         }
-        const C* vt = static_cast<const C*>(ps.vtab[ps.orient[blockIdx.z]]);
+        const C* vt = static_cast<const C*>(ps.vtab_item[blockIdx.z] ? ps.vtab_item[blockIdx.z]
+                                                                       : ps.vtab[ps.orient[blockIdx.z]]);
         const C v = vt ? (i0 + c < g.inner_valid
                               ? vt[(long long)blockIdx.y * g.ms + (long long)j * g.S + i0 + c]
                               : C{0, 0})
@@ -305,7 +306,9 @@ __global__ void k_vtable(typename CxOf<R>::T* __restrict__ V, const __grid_const
         long long rest = e;
         const int last = (int)(rest % nhalf);
         rest /= nhalf;
-        if (p.ndim == 2) {
+        if (p.ndim == 1) {
+            k[0] = last;
+        } else if (p.ndim == 2) {
             k[0] = (int)rest;
             k[1] = last;
         } else {
@@ -326,7 +329,8 @@ template <typename R, int RAD, int MAXT>
 __global__ void __launch_bounds__(MAXT)
 k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
                const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
-               const __grid_constant__ SymbolParams p, int* status) {
+               const __grid_constant__ SymbolParams p, int* status,
+               const __grid_constant__ RowTables rt) {
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
@@ -360,11 +364,18 @@ k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
     }
     __syncthreads();
     // Y[k] = V[k] X[k]
-    ColSymbol<RAD> cs;
-    int kz[3] = {0, 0, 0};
-    col_symbol_init<RAD>(p, kz, cs);
-    apply_multiplier<RAD>(v, sm, j, q, p, cs, 0, 0);
-    if (j == 0) xn = multiply_single<C>(xn, p, n, 0, 0);
+    const C* vt = row < kMaxItems ? static_cast<const C*>(rt.t[row]) : nullptr;
+    if (vt) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], __ldg(vt + j + q * r));
+        if (j == 0) xn = cmul(xn, __ldg(vt + n));
+    } else {
+        ColSymbol<RAD> cs;
+        int kz[3] = {0, 0, 0};
+        col_symbol_init<RAD>(p, kz, cs);
+        apply_multiplier<RAD>(v, sm, j, q, p, cs, 0, 0);
+        if (j == 0) xn = multiply_single<C>(xn, p, n, 0, 0);
+    }
     __syncthreads();
     // inverse split: Z'[k] = (Y[k] + conj Y[n-k]) + i conj(W^k) (Y[k] - conj Y[n-k])
 #pragma unroll
@@ -518,7 +529,8 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
         k[1] = blockIdx.y;
         k[2] = i0 + c;
     }
-    const C* vt = static_cast<const C*>(ps.vtab[ps.orient[blockIdx.z]]);
+    const C* vt = static_cast<const C*>(ps.vtab_item[blockIdx.z] ? ps.vtab_item[blockIdx.z]
+                                                                   : ps.vtab[ps.orient[blockIdx.z]]);
     if (vt) {
         // multipliers shared by every solve of this shape and T, built once per run
         const C* vbase = vt + (long long)blockIdx.y * g.ms + i0 + c;
@@ -615,7 +627,7 @@ static int col_threads_cap() {
 template <typename R, int RAD, int MAXT>
 static cudaError_t launch_fused_1d_reg_t(R* grid, int n_log2, int nrows, const void* tw,
                                          int twn_log2, const SymbolParams& p, int* status,
-                                         cudaStream_t s) {
+                                         const RowTables& rt, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << n_log2;
     const int rpc = reg_rows_per_cta(n_log2);
@@ -625,18 +637,19 @@ static cudaError_t launch_fused_1d_reg_t(R* grid, int n_log2, int nrows, const v
     if (err != cudaSuccess) return err;
     const int blocks = (nrows + rpc - 1) / rpc;
     k_fused_1d_reg<R, RAD, MAXT><<<blocks, threads, smem, s>>>(
-        grid, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2, p, status);
+        grid, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2, p, status, rt);
     return cudaGetLastError();
 }
 
 template <typename R, int RAD>
 static cudaError_t launch_fused_1d_reg_r(R* grid, int n_log2, int nrows, const void* tw,
                                          int twn_log2, const SymbolParams& p, int* status,
-                                         cudaStream_t s) {
+                                         const RowTables& rt, cudaStream_t s) {
     if ((1 << (n_log2 - 4)) <= 256)
-        return launch_fused_1d_reg_t<R, RAD, 256>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+        return launch_fused_1d_reg_t<R, RAD, 256>(grid, n_log2, nrows, tw, twn_log2, p, status, rt,
+                                                  s);
     return launch_fused_1d_reg_t<R, RAD, MaxT<R>::v>(grid, n_log2, nrows, tw, twn_log2, p, status,
-                                                     s);
+                                                     rt, s);
 }
 
 template <typename R, int MAXT>
@@ -722,17 +735,21 @@ static cudaError_t launch_cols_fused_reg_r(void* H, const ColGeom& g, const void
 
 template <typename R>
 cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
-                            const SymbolParams& p, int* status, cudaStream_t s) {
+                            const SymbolParams& p, int* status, cudaStream_t s,
+                            const RowTables* rtab) {
     using C = typename CxOf<R>::T;
     const int n = 1 << n_log2;
+    RowTables rt;
+    for (int i = 0; i < kMaxItems; ++i) rt.t[i] = rtab ? rtab->t[i] : nullptr;
     if (n_log2 >= 4 && (n >> 4) <= MaxT<R>::v) {
         switch (p.r) {
-            case 0: return launch_fused_1d_reg_r<R, 0>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
-            case 1: return launch_fused_1d_reg_r<R, 1>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
-            case 2: return launch_fused_1d_reg_r<R, 2>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
-            default: return launch_fused_1d_reg_r<R, 3>(grid, n_log2, nrows, tw, twn_log2, p, status, s);
+            case 0: return launch_fused_1d_reg_r<R, 0>(grid, n_log2, nrows, tw, twn_log2, p, status, rt, s);
+            case 1: return launch_fused_1d_reg_r<R, 1>(grid, n_log2, nrows, tw, twn_log2, p, status, rt, s);
+            case 2: return launch_fused_1d_reg_r<R, 2>(grid, n_log2, nrows, tw, twn_log2, p, status, rt, s);
+            default: return launch_fused_1d_reg_r<R, 3>(grid, n_log2, nrows, tw, twn_log2, p, status, rt, s);
         }
     }
+    if (rtab) return cudaErrorInvalidValue;   // tables need the register kernels (n >= 16)
     const int rpc = rows_per_cta_for(n_log2, sizeof(C), MaxT<R>::v);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
     const int threads = threads_for((long long)rpc * n, MaxT<R>::v);
@@ -883,7 +900,7 @@ cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_h
 
 #define SFFT_INSTANTIATE(R)                                                                        \
     template cudaError_t launch_fused_1d<R>(R*, int, int, const void*, int, const SymbolParams&,   \
-                                            int*, cudaStream_t);                                   \
+                                            int*, cudaStream_t, const RowTables*);                 \
     template cudaError_t launch_rows_r2c<R>(const R*, void*, long long, int, int, const void*,     \
                                             int, cudaStream_t);                                    \
     template cudaError_t launch_rows_c2r<R>(const void*, R*, long long, int, int, const void*,     \

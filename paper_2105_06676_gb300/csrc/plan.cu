@@ -167,20 +167,25 @@ static cudaError_t alloc_tables(stencil_plan_s* p) {
     const size_t celem = p->precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
     err = cudaMalloc(&p->tw, celem << p->twn_log2);
     if (err != cudaSuccess) return err;
-    err = p->precision == STENCIL_FP32 ? launch_twiddles<float>(p->tw, p->twn_log2, 0)
-                                       : launch_twiddles<double>(p->tw, p->twn_log2, 0);
+    // tables are built on the per-thread stream and awaited there, so creating a
+    // plan never waits for work other streams have in flight
+    const cudaStream_t ts = cudaStreamPerThread;
+    err = p->precision == STENCIL_FP32 ? launch_twiddles<float>(p->tw, p->twn_log2, ts)
+                                       : launch_twiddles<double>(p->tw, p->twn_log2, ts);
     if (err != cudaSuccess) return err;
     for (int a = 0; a < p->ndim; ++a) {
         err = cudaMalloc(&p->E64[a], sizeof(double2) * p->dims[a]);
         if (err != cudaSuccess) return err;
         err = cudaMalloc(&p->E32[a], sizeof(float2) * p->dims[a]);
         if (err != cudaSuccess) return err;
-        err = launch_axis_table(p->E64[a], p->E32[a], (int)p->dims[a], 0);
+        err = launch_axis_table(p->E64[a], p->E32[a], (int)p->dims[a], ts);
         if (err != cudaSuccess) return err;
     }
     err = cudaMalloc(&p->status, sizeof(int));
     if (err != cudaSuccess) return err;
-    err = cudaMemset(p->status, 0, sizeof(int));
+    err = cudaMemsetAsync(p->status, 0, sizeof(int), ts);
+    p->dev_bytes += (celem << p->twn_log2) + sizeof(int);
+    for (int a = 0; a < p->ndim; ++a) p->dev_bytes += (sizeof(double2) + sizeof(float2)) * p->dims[a];
     return err;
 }
 
@@ -215,7 +220,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
                           void* H, long long Mp, const int* orient, const int (*perms)[3],
                           int norient, const void* tw, int twn_log2, const double2* const* E64,
                           const float2* const* E32, int* status, cudaStream_t s,
-                          const void* const* vtabs) {
+                          const void* const* vtabs, const void* const* vitems) {
     const int d = p->ndim;
     if (items < 1 || items > kMaxItems || norient < 1 || norient > kMaxOrient)
         return cudaErrorInvalidValue;
@@ -225,6 +230,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         ss.p[o] = make_symbol_params(p, len, T, E64, E32, perms ? perms[o] : nullptr);
     for (int i = 0; i < items; ++i) ss.orient[i] = orient ? orient[i] : 0;
     for (int o = 0; o < norient; ++o) ss.vtab[o] = vtabs ? vtabs[o] : nullptr;
+    for (int i = 0; i < items; ++i) ss.vtab_item[i] = vitems ? vitems[i] : nullptr;
     const int maxt = sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64;
     const int celem = 2 * sizeof(R);
     const int n_log2 = ilog2_exact(len[d - 1]) - 1;
@@ -232,8 +238,10 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     cudaError_t err;
     if (d == 1) {
         // every item of a 1-D batch has the one orientation
-        PROF_LAUNCH(PASS_FUSED_1D,
-                    launch_fused_1d<R>(S, n_log2, items, tw, twn_log2, ss.p[0], status, s));
+        RowTables rt;
+        for (int i = 0; i < kMaxItems; ++i) rt.t[i] = ss.vtab_item[i];
+        PROF_LAUNCH(PASS_FUSED_1D, launch_fused_1d<R>(S, n_log2, items, tw, twn_log2, ss.p[0],
+                                                      status, s, vitems ? &rt : nullptr));
         return cudaSuccess;
     }
     const int64_t rows_item = d == 2 ? len[0] : len[0] * len[1];
@@ -284,7 +292,7 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
                            const double2* const* E64, const float2* const* E32, int* status,
                            cudaStream_t s) {
     return batched_solve<R>(p, grid, len, 1, T, H, Mp, nullptr, nullptr, 1, tw, twn_log2, E64, E32,
-                            status, s, nullptr);
+                            status, s, nullptr, nullptr);
 }
 
 #define SFFT_SOLVE_INST(R)                                                                         \
@@ -295,7 +303,7 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
                                           void*, long long, const int*, const int (*)[3], int,     \
                                           const void*, int, const double2* const*,                 \
                                           const float2* const*, int*, cudaStream_t,                \
-                                          const void* const*);
+                                          const void* const*, const void* const*);
 SFFT_SOLVE_INST(float)
 SFFT_SOLVE_INST(double)
 
@@ -397,10 +405,11 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
         p->Mp = (n + 1 + align - 1) / align * align;
         if (p->H_bytes) {
             err = cudaMalloc(&p->H, p->H_bytes);
-            if (err == cudaSuccess) err = cudaMemset(p->H, 0, p->H_bytes);
+            if (err == cudaSuccess) err = cudaMemsetAsync(p->H, 0, p->H_bytes, cudaStreamPerThread);
+            p->dev_bytes += p->H_bytes;
         }
     }
-    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err == cudaSuccess) err = cudaStreamSynchronize(cudaStreamPerThread);
     if (err != cudaSuccess) {
         free_plan(p);
         return from_cuda(err);
@@ -437,6 +446,7 @@ int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int6
             p->dev_grid = nullptr;
             return from_cuda(err);
         }
+        p->dev_bytes += bytes;
     }
     err = cudaMemcpyAsync(p->dev_grid, host_in, bytes, cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return from_cuda(err);
@@ -463,10 +473,12 @@ int stencil_status(stencil_plan_t p, void* stream) {
     cudaError_t err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return from_cuda(err);
     int flag = 0;
-    err = cudaMemcpy(&flag, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+    err = cudaMemcpyAsync(&flag, p->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return from_cuda(err);
     if (flag) {
-        err = cudaMemset(p->status, 0, sizeof(int));
+        err = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return from_cuda(err);
         return STENCIL_ENONFINITE;
     }
@@ -481,6 +493,19 @@ int stencil_destroy(stencil_plan_t p) {
 }
 
 }  // extern "C"
+
+namespace sfft {
+// Replace a plan's weights (same radius bound); captured graphs hold the old
+// weights in their kernel parameters and are dropped.
+void plan_set_weights(stencil_plan_s* p, int radius, const double* w) {
+    p->radius = radius;
+    p->nweights = 1;
+    for (int a = 0; a < p->ndim; ++a) p->nweights *= 2 * radius + 1;
+    for (int i = 0; i < p->nweights; ++i) p->weights[i] = w[i];
+    p->real_symbol = symmetric_weights(p->weights, p->ndim, radius);
+    aperiodic_forget_graphs(p);
+}
+}  // namespace sfft
 
 extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     if (!p || (cutoff != 0 && cutoff < 2)) return STENCIL_EINVAL;

@@ -73,10 +73,13 @@ struct stencil_plan_s {
     AperiodicState* ap = nullptr;
     int64_t cutoff = 0;  // 0: automatic
     Profiler prof;
+    bool use_graphs = true;   // replay zero-Dirichlet runs as CUDA graphs
+    size_t dev_bytes = 0;     // device memory this plan holds
 };
 
 namespace sfft {
 int ilog2_exact(int64_t v);
+void plan_set_weights(stencil_plan_s* p, int radius, const double* w);
 int64_t max_axis(int ndim, int precision, int axis);
 SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
                                 const double2* const* E64, const float2* const* E32,
@@ -87,7 +90,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
                           void* H, long long Mp, const int* orient, const int (*perms)[3],
                           int norient, const void* tw, int twn_log2, const double2* const* E64,
                           const float2* const* E32, int* status, cudaStream_t s,
-                          const void* const* vtabs);
+                          const void* const* vtabs, const void* const* vitems = nullptr);
 template <typename R>
 cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
                            void* H, long long Mp, const void* tw, int twn_log2,
@@ -97,3 +100,7 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
 
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
 void aperiodic_release(stencil_plan_s* p);
+// drop captured graphs (their kernel parameters hold the plan's weights)
+void aperiodic_forget_graphs(stencil_plan_s* p);
+// device bytes held by the zero-Dirichlet machinery of a plan
+size_t aperiodic_bytes(const stencil_plan_s* p);

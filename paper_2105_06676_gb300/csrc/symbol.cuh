@@ -57,6 +57,13 @@ struct SymbolSet {
     // optional precomputed multipliers V = Lambda^T / N per orientation, laid
     // out like one item's half spectrum (null: evaluate on the fly)
     const void* vtab[kMaxOrient];
+    // optional per-item tables (each item its own weights and T); override vtab
+    const void* vtab_item[kMaxItems];
+};
+
+// Per-row multiplier tables of a batched 1-D solve (row r uses t[r] when set).
+struct RowTables {
+    const void* t[kMaxItems];
 };
 
 // sum_m w[m] prod_a E_a[(m_a k_a) mod l_a], separably; k[a] in [0, l_a).

@@ -146,3 +146,30 @@ def test_graph_replay_matches_eager_run(dims, r, T):
     plan.close()
     ref = oracle.stencil_loop(a0.double().cpu().numpy(), w, T, "dirichlet")
     assert err_rel(first.double().cpu().numpy(), ref, a0.cpu().numpy()) <= 2e-4
+
+
+def test_concurrent_plans_on_separate_streams():
+    # freshly created plans of different shapes, run at once on non-blocking
+    # streams, must give the same results as one at a time (each plan's first
+    # run uploads its tables; no kernel may read them before they land)
+    from paper_2105_06676_gb300 import StencilPlan
+    cases = [((4096,), 2, 3), ((1024,), 1, 16), ((64, 32), 2, 5), ((16, 8, 16), 1, 5),
+             ((512,), 1, 185), ((128, 128), 1, 40), ((32, 32, 32), 1, 9)]
+    streams = [torch.cuda.Stream() for _ in cases]
+    runs = []
+    for k, (dims, r, T) in enumerate(cases):
+        w = wl.weights_random_box(len(dims), r, 60 + k)
+        a0 = wl.grid_uniform(dims, 70 + k)
+        prec = "fp64" if k % 2 else "fp32"
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        runs.append((StencilPlan(dims, w, "dirichlet", prec), torch.tensor(a0, dtype=dt, device="cuda"),
+                     a0, w, T, prec))
+    torch.cuda.synchronize()
+    for s, (plan, g, a0, w, T, prec) in zip(streams, runs):
+        with torch.cuda.stream(s):
+            plan.run(g, T, stream=s)
+    torch.cuda.synchronize()
+    for plan, g, a0, w, T, prec in runs:
+        ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+        assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[prec], (a0.shape, T)
+        plan.close()

@@ -1,0 +1,129 @@
+"""The serving loop (stencil_server_*): mixed requests, continuous batching,
+admission by device-memory budget, errors. Each served result must equal the
+same request solved alone (stencil_plan + stencil_run) within the solver's
+tolerance, and the alone result must match the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06676_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 2e-4}
+
+
+def alone(a0, w, T, boundary, precision):
+    from paper_2105_06676_gb300 import StencilPlan
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(a0.shape, w, boundary, precision)
+    plan.run(g, T)
+    assert plan.status() == 0
+    plan.close()
+    return g.double().cpu().numpy()
+
+
+def mixed_requests(n, seed, max_cells=1 << 14):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nd = int(rng.integers(1, 4))
+        if nd == 1:
+            dims = (int(2 ** rng.integers(6, 13)),)
+        elif nd == 2:
+            dims = tuple(int(2 ** rng.integers(4, 8)) for _ in range(2))
+        else:
+            dims = tuple(int(2 ** rng.integers(3, 5)) for _ in range(3))
+        r = int(rng.integers(1, 3))
+        if min(dims) < 2 * r + 1:
+            r = 1
+        w = wl.weights_random_box(nd, r, 100 + i)
+        T = int(10 ** rng.uniform(0.5, 2.5))
+        boundary = "periodic" if rng.random() < 0.5 else "dirichlet"
+        precision = "fp32" if rng.random() < 0.7 else "fp64"
+        out.append((wl.grid_uniform(dims, 200 + i), w, T, boundary, precision))
+    return out
+
+
+def test_mixed_stream_matches_alone_and_oracle():
+    from paper_2105_06676_gb300 import StencilServer
+    reqs = mixed_requests(48, 7)
+    # a burst of small periodic 2-D requests of one shape: these get batched
+    for i in range(12):
+        reqs.append((wl.grid_uniform((64, 64), 900 + i), wl.weights_random_box(2, 1 + i % 2, 50 + i),
+                     int(5 + 7 * i), "periodic", "fp32"))
+    srv = StencilServer(hbm_budget_bytes=8 << 30, max_slots=6)
+    grids, tickets = [], []
+    for a0, w, T, b, prec in reqs:
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        g = torch.tensor(a0, dtype=dt, device="cuda")
+        grids.append(g)
+    torch.cuda.synchronize()
+    for g, (a0, w, T, b, prec) in zip(grids, reqs):
+        tickets.append(srv.submit(g, w, T, b))
+    for t in tickets:
+        rc, lat = srv.wait(t, 120.0)
+        assert rc == 0 and lat > 0
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["max_in_flight"] >= 2           # work overlapped on the device
+    assert st["batched_launches"] >= 1 and st["batched_requests"] >= 2
+    for g, (a0, w, T, b, prec) in zip(grids, reqs):
+        got = g.double().cpu().numpy()
+        ref_alone = alone(a0, w, T, b, prec)
+        scale = np.max(np.abs(a0))
+        assert np.max(np.abs(got - ref_alone)) / scale <= TOL[prec], (a0.shape, T, b, prec)
+        if a0.size * T <= 2e6:
+            ref = oracle.stencil_loop(a0, w, T, b)
+            assert np.max(np.abs(got - ref)) / scale <= TOL[prec], (a0.shape, T, b, prec)
+
+
+def test_small_budget_serialises_admission():
+    from paper_2105_06676_gb300 import StencilServer
+    dims = (512, 512)                        # above the batching size: one plan per request
+    w = wl.weights_star(2, 0.6, 0.1)
+    # room for one periodic 512^2 FP32 plan (about 1.14 MB of tables and workspace), not two
+    srv = StencilServer(hbm_budget_bytes=1_500_000, max_slots=4)
+    a0s = [wl.grid_uniform(dims, 10 + i) for i in range(6)]
+    gs = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in a0s]
+    torch.cuda.synchronize()
+    ts = [srv.submit(g, w, 300 + i, "periodic") for i, g in enumerate(gs)]
+    for t in ts:
+        assert srv.wait(t, 60.0)[0] == 0
+    st = srv.stats()
+    srv.close()
+    assert st["max_in_flight"] == 1 and st["peak_bytes"] <= 1_500_000
+    for i, (g, a0) in enumerate(zip(gs, a0s)):
+        ref = alone(a0, w, 300 + i, "periodic", "fp32")
+        assert np.max(np.abs(g.double().cpu().numpy() - ref)) <= 2e-4
+
+
+def test_request_that_never_fits_fails_with_enomem():
+    from paper_2105_06676_gb300 import StencilServer
+    srv = StencilServer(hbm_budget_bytes=1000, max_slots=2)
+    g = torch.rand((512, 512), dtype=torch.float32, device="cuda")
+    t = srv.submit(g, wl.weights_star(2, 0.6, 0.1), 10, "periodic")
+    rc, _ = srv.wait(t, 30.0)
+    assert rc == -2
+    srv.close()
+
+
+def test_queue_full_and_invalid_requests():
+    from paper_2105_06676_gb300 import StencilServer
+    srv = StencilServer(hbm_budget_bytes=8 << 30, max_slots=1, queue_capacity=1)
+    big = torch.rand((2048, 2048), dtype=torch.float32, device="cuda")
+    w9 = wl.weights_random_box(2, 1, 3)
+    copies = [big.clone() for _ in range(3)]
+    torch.cuda.synchronize()
+    codes = [srv.try_submit(c, w9, 2048, "dirichlet")[0] for c in copies]
+    assert -6 in codes                      # STENCIL_EQUEUEFULL
+    bad = torch.rand((12, 16), dtype=torch.float32, device="cuda")
+    assert srv.try_submit(bad, wl.weights_star(2, 0.6, 0.1), 5)[0] == -7   # not a power of two
+    tiny = torch.rand((2, 8), dtype=torch.float32, device="cuda")
+    assert srv.try_submit(tiny, wl.weights_star(2, 0.6, 0.1), 5)[0] == -1  # axis below 4
+    srv.close()                              # drains what was queued
