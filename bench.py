@@ -166,6 +166,89 @@ def time_solve(plan, grid, pristine, flush, K, W, T):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+def serve_mixed_stream(n_requests: int, seed: int = 5000):
+    """Mixed solve stream through the server (FP32 passes, FP64 Lambda^T).
+
+    Sizes capped to the single-pass limits both paths share: 1-D l <= 2^14, 2-D per-axis
+    <= 2^11, 3-D per-axis <= 2^7; T log-uniform in [10, 1e5]; boundary 50/50;
+    radius 1-2 box with random weights summing to 1. First the capacity (all
+    requests queued at once), then a Poisson replay at 0.8x that rate for
+    p50/p99 latency, then the plain FP64 one-request-at-a-time path.
+    """
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2105_06676_gb300 import StencilPlan, StencilServer
+    from paper_2105_06676_gb300 import workloads as wl
+
+    reqs = wl.mixed_stream(n_requests, 1.0, seed, max_1d_log2=14, max_2d_log2=11, max_3d_log2=7)
+    inputs = [torch.tensor(wl.grid_uniform(r.dims, r.grid_seed), dtype=torch.float32, device="cuda")
+              for r in reqs]
+    updates = sum(int(np.prod(r.dims)) * r.T for r in reqs)
+
+    def run_server(arrivals):
+        grids = [x.clone() for x in inputs]
+        torch.cuda.synchronize()
+        srv = StencilServer(hbm_budget_bytes=64 << 30, max_slots=8, queue_capacity=1 << 20)
+        tickets = [None] * len(reqs)
+
+        def producer():
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                if arrivals is not None:
+                    delay = arrivals[i] - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets[i] = srv.submit(grids[i], r.weights, r.T, r.boundary)
+
+        t0 = time.perf_counter()
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        lats = []
+        for t in tickets:
+            rc, lat = srv.wait(t, 600.0)
+            assert rc == 0, rc
+            lats.append(lat)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return wall, np.array(lats), st
+
+    # warm the plan pool, then measure capacity with everything queued at once
+    run_server(None)
+    wall_cap, lat_cap, st = run_server(None)
+    rate = 0.8 * len(reqs) / wall_cap
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    wall, lats, st = run_server(arrivals)
+
+    # plain FP64 path, one request at a time (plan, solve, synchronise)
+    grids64 = [x.double() for x in inputs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, r in zip(grids64, reqs):
+        plan = StencilPlan(r.dims, r.weights, r.boundary, "fp64")
+        plan.run(g, r.T)
+        torch.cuda.synchronize()
+        plan.close()
+    wall64 = time.perf_counter() - t0
+    return {
+        "requests": len(reqs), "updates": updates,
+        "capacity_req_per_s": len(reqs) / wall_cap,
+        "value": updates / wall_cap, "unit": "point-updates/s",
+        "poisson_rate_req_per_s": rate,
+        "p50_ms": float(np.percentile(lats, 50) * 1e3), "p99_ms": float(np.percentile(lats, 99) * 1e3),
+        "poisson_point_updates_per_s": updates / wall,
+        "fp64_one_at_a_time": {"value": updates / wall64, "wall_s": wall64},
+        "max_in_flight": st["max_in_flight"], "batched_launches": st["batched_launches"],
+        "batched_requests": st["batched_requests"],
+        "sizes": "1-D <= 2^14, 2-D <= 2048^2, 3-D <= 128^3 (single-pass limits of this build)",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +258,7 @@ def main():
     ap.add_argument("--ref-steps-per-sample", type=int, default=100)
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -246,6 +330,9 @@ def main():
     del gd, pris_d
     pland.close()
 
+    # ---- serving: mixed stream through the continuous-batching server
+    serving = serve_mixed_stream(args.serve_requests) if args.serve_requests > 0 else None
+
     # ---- e2e through the C ABI with pinned host buffers (H2D + solve + D2H per step)
     host_in = torch.tensor(a0, dtype=torch.float32).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -306,6 +393,7 @@ def main():
                          "peak_source": peak_kind,
                          "per_kernel_ms": {k: round(v, 5) for k, v in avg_ms.items()},
                          "algorithmic_bytes": algo[dominant]},
+            "serving": serving,
             "gpu_launches": int(round(step_kernel_launches * args.steps)),
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -154,6 +154,10 @@ const char* stencil_profile_kind_name(int kind);
  *   2, step                            -- scatter of that step's kept cells
  *   3, T_b, n, then per tile: (lo, hi) for each of 3 axes
  *                                      -- base case over output tiles
+ *   4, T_c                             -- T_c steps of the loop on the whole grid
+ *   5, T                               -- T single steps of the loop on the whole grid
+ * With cutoff 0 the schedule is the one the solver runs: RecursiveBoundary, or
+ * the plain loop (records 4 / 5 only) when its estimated cost is lower.
  * Axes beyond ndim are reported with extent 1. A strip's box cell q maps to
  * grid cell off + q when q < valid on every axis; a scatter writes the cells
  * with lo < dist <= hi and, when face_axis >= 0, distance to that face <= hi.

@@ -144,7 +144,15 @@ struct BaseParams {
     int Tb;
     int wout;         // write cells with dist <= wout
     double w[kMaxWeights];
+    float wf[kMaxWeights];
 };
+
+template <typename R>
+__device__ __forceinline__ R base_weight(const BaseParams& p, int i);
+template <>
+__device__ __forceinline__ float base_weight<float>(const BaseParams& p, int i) { return p.wf[i]; }
+template <>
+__device__ __forceinline__ double base_weight<double>(const BaseParams& p, int i) { return p.w[i]; }
 
 template <typename R, int RAD>
 __global__ void __launch_bounds__(512)
@@ -308,6 +316,155 @@ k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
     }
 }
 
+// 1-D and 3-D base cases with the same zero-ring layout as k_base_2d (no
+// bounds tests in the stencil loop, no divisions per cell).
+template <typename R, int RAD>
+__global__ void __launch_bounds__(256)
+k_base_1d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict__ tiles,
+          const __grid_constant__ BaseParams p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int W = 2 * RAD + 1;
+    const BaseTile t = tiles[blockIdx.x];
+    const int L = p.gdims[0];
+    const int h = RAD * p.Tb;
+    const int i0 = max(t.lo[0] - h, 0), i1 = min(t.hi[0] + h, L);
+    const int ex = i1 - i0;
+    const int cells = ex + 2 * RAD;
+    R* b0 = reinterpret_cast<R*>(smraw);
+    R* b1 = b0 + cells;
+    for (int e = threadIdx.x; e < 2 * cells; e += blockDim.x) b0[e] = R(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ex; e += blockDim.x) b0[e + RAD] = X[i0 + e];
+    R w[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = (R)p.w[i];
+    __syncthreads();
+    for (int step = 1; step <= p.Tb; ++step) {
+        const int reach = (p.Tb - step) * RAD;
+        const int c0 = max(t.lo[0] - reach, i0) - i0, c1 = min(t.hi[0] + reach, i1) - i0;
+        for (int x = c0 + threadIdx.x; x < c1; x += blockDim.x) {
+            R acc = 0;
+#pragma unroll
+            for (int m = 0; m < W; ++m) acc += w[m] * b0[x + m];
+            b1[x + RAD] = acc;
+        }
+        __syncthreads();
+        R* tmp = b0;
+        b0 = b1;
+        b1 = tmp;
+    }
+    for (int g = t.lo[0] + threadIdx.x; g < t.hi[0]; g += blockDim.x) {
+        const int d = min(g + 1, L - g);
+        if (d <= p.wout) Y[g] = b0[g - i0 + RAD];
+    }
+}
+
+template <typename R, int RAD>
+__global__ void __launch_bounds__(256)
+k_base_3d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict__ tiles,
+          const __grid_constant__ BaseParams p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int W = 2 * RAD + 1;
+    const BaseTile t = tiles[blockIdx.x];
+    const int L0 = p.gdims[0], L1 = p.gdims[1], L2 = p.gdims[2];
+    const int h = RAD * p.Tb;
+    int lo[3], hi[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = max(t.lo[a] - h, 0);
+        hi[a] = min(t.hi[a] + h, p.gdims[a]);
+        ext[a] = hi[a] - lo[a];
+    }
+    const int px = ext[2] + 2 * RAD, py = ext[1] + 2 * RAD;
+    const int plane = px * py;
+    const int cells = (ext[0] + 2 * RAD) * plane;
+    R* b0 = reinterpret_cast<R*>(smraw);
+    R* b1 = b0 + cells;
+    for (int e = threadIdx.x; e < 2 * cells; e += blockDim.x) b0[e] = R(0);
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+    for (int zy = ty; zy < ext[0] * ext[1]; zy += ny) {
+        const int z = zy / ext[1], y = zy - z * ext[1];
+        for (int x = tx; x < ext[2]; x += 32)
+            b0[(z + RAD) * plane + (y + RAD) * px + x + RAD] =
+                X[((long long)(lo[0] + z) * L1 + lo[1] + y) * L2 + lo[2] + x];
+    }
+    __syncthreads();
+    for (int step = 1; step <= p.Tb; ++step) {
+        const int reach = (p.Tb - step) * RAD;
+        int c0[3], c1[3];
+        for (int a = 0; a < 3; ++a) {
+            c0[a] = max(t.lo[a] - reach, lo[a]) - lo[a];
+            c1[a] = min(t.hi[a] + reach, hi[a]) - lo[a];
+        }
+        const int cy = c1[1] - c0[1], cz = c1[0] - c0[0];
+        for (int zy = ty; zy < cz * cy; zy += ny) {
+            const int z = c0[0] + zy / cy, y = c0[1] + zy % cy;
+            for (int x = c0[2] + tx; x < c1[2]; x += 32) {
+                const R* src = b0 + z * plane + y * px + x;
+                R acc = 0;
+#pragma unroll
+                for (int m0 = 0; m0 < W; ++m0)
+#pragma unroll
+                    for (int m1 = 0; m1 < W; ++m1)
+#pragma unroll
+                        for (int m2 = 0; m2 < W; ++m2)
+                            acc += base_weight<R>(p, (m0 * W + m1) * W + m2) *
+                                   src[m0 * plane + m1 * px + m2];
+                b1[(z + RAD) * plane + (y + RAD) * px + x + RAD] = acc;
+            }
+        }
+        __syncthreads();
+        R* tmp = b0;
+        b0 = b1;
+        b1 = tmp;
+    }
+    const int oy = t.hi[1] - t.lo[1], oz = t.hi[0] - t.lo[0];
+    for (int zy = ty; zy < oz * oy; zy += ny) {
+        const int gz = t.lo[0] + zy / oy, gy = t.lo[1] + zy % oy;
+        for (int gx = t.lo[2] + tx; gx < t.hi[2]; gx += 32) {
+            const int d = min(min(min(gz + 1, L0 - gz), min(gy + 1, L1 - gy)), min(gx + 1, L2 - gx));
+            if (d > p.wout) continue;
+            Y[((long long)gz * L1 + gy) * L2 + gx] =
+                b0[(gz - lo[0] + RAD) * plane + (gy - lo[1] + RAD) * px + gx - lo[2] + RAD];
+        }
+    }
+}
+
+// One step of the loop on the whole 3-D grid with zero ghosts (a single
+// launch per step; used when the boundary region is the whole grid).
+template <typename R, int RAD>
+__global__ void __launch_bounds__(256)
+k_step_3d(const R* __restrict__ A, R* __restrict__ B, const __grid_constant__ BaseParams p) {
+    constexpr int W = 2 * RAD + 1;
+    const int L0 = p.gdims[0], L1 = p.gdims[1], L2 = p.gdims[2];
+    const long long n = (long long)L0 * L1 * L2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e % L2);
+        const long long zy = e / L2;
+        const int y = (int)(zy % L1), z = (int)(zy / L1);
+        R acc = 0;
+#pragma unroll
+        for (int m0 = 0; m0 < W; ++m0) {
+            const int zz = z + m0 - RAD;
+            if (zz < 0 || zz >= L0) continue;
+#pragma unroll
+            for (int m1 = 0; m1 < W; ++m1) {
+                const int yy = y + m1 - RAD;
+                if (yy < 0 || yy >= L1) continue;
+                const R* row = A + ((long long)zz * L1 + yy) * L2;
+#pragma unroll
+                for (int m2 = 0; m2 < W; ++m2) {
+                    const int xx = x + m2 - RAD;
+                    if (xx >= 0 && xx < L2)
+                        acc += base_weight<R>(p, (m0 * W + m1) * W + m2) * __ldg(row + xx);
+                }
+            }
+        }
+        B[e] = acc;
+    }
+}
+
 // 2-D gather and scatter of batch items in 32 x 32 tiles of the box. A
 // transposed item (perm = (1, 0)) goes through a shared tile so that both the
 // grid side and the box side are accessed along their contiguous axis.
@@ -435,9 +592,13 @@ struct Step {                  // all periodic solves of one P1 or P2 step
 };
 
 struct Op {
-    enum Kind { SOLVE, SCATTER, BASE } kind;
-    int step;                  // SOLVE / SCATTER
-    int64_t T;                 // BASE: steps
+    // SOLVE / SCATTER: a periodic strip solve and its write-back (step index);
+    // BASE: a RecursiveBoundary leaf, T steps of the loop on the frame;
+    // LOOP: T steps of the loop on the whole grid (temporally blocked tiles);
+    // STEP: T single-step launches of the loop on the whole grid (3-D)
+    enum Kind { SOLVE, SCATTER, BASE, LOOP, STEP } kind;
+    int step;
+    int64_t T;
 };
 
 struct BaseSet {
@@ -450,6 +611,7 @@ struct Schedule {
     std::vector<Step> steps;
     std::vector<Op> ops;
     std::vector<VTable> tables;
+    bool loop = false;         // the plain loop over the whole grid (no interior solve)
 };
 
 struct LevelBuffers {
@@ -573,36 +735,55 @@ static void build_rb(const stencil_plan_s* p, Schedule& sc, int64_t T, int level
         return;
     }
     const int64_t T1 = T / 2, T2 = T - T1;
+    // the largest dist in the grid: a keep range starting at or above it is empty
+    int64_t maxdist = p->dims[0] - p->dims[0] / 2;
+    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] - p->dims[a] / 2);
     // Step 1: P1 over dist <= 2 sigma T for T1 steps, kept on (sigma T1, sigma T + sigma T2]
-    Step s1;
-    s1.level = level;
-    s1.T = T1;
-    s1.batches = make_batches(p, 2 * sigma * T, (int)(sigma * T1),
-                              (int)std::min<int64_t>(sigma * T + sigma * T2, kNoHi));
-    sc.steps.push_back(s1);
-    const int i1 = (int)sc.steps.size() - 1;
-    sc.ops.push_back(Op{Op::SOLVE, i1, 0});
+    int i1 = -1;
+    if (sigma * T1 < maxdist) {
+        Step s1;
+        s1.level = level;
+        s1.T = T1;
+        s1.batches = make_batches(p, 2 * sigma * T, (int)(sigma * T1),
+                                  (int)std::min<int64_t>(sigma * T + sigma * T2, kNoHi));
+        sc.steps.push_back(s1);
+        i1 = (int)sc.steps.size() - 1;
+        sc.ops.push_back(Op{Op::SOLVE, i1, 0});
+    }
     build_rb(p, sc, T1, level + 1, cutoff);
-    sc.ops.push_back(Op{Op::SCATTER, i1, 0});
+    if (i1 >= 0) sc.ops.push_back(Op{Op::SCATTER, i1, 0});
     // Step 2: P2 over dist <= sigma T + sigma T2 for T2 steps, kept on (sigma T2, sigma T]
-    Step s2;
-    s2.level = level;
-    s2.T = T2;
-    s2.batches = make_batches(p, sigma * T + sigma * T2, (int)(sigma * T2), (int)(sigma * T));
-    sc.steps.push_back(s2);
-    const int i2 = (int)sc.steps.size() - 1;
-    sc.ops.push_back(Op{Op::SOLVE, i2, 0});
+    int i2 = -1;
+    if (sigma * T2 < maxdist) {
+        Step s2;
+        s2.level = level;
+        s2.T = T2;
+        s2.batches = make_batches(p, sigma * T + sigma * T2, (int)(sigma * T2), (int)(sigma * T));
+        sc.steps.push_back(s2);
+        i2 = (int)sc.steps.size() - 1;
+        sc.ops.push_back(Op{Op::SOLVE, i2, 0});
+    }
     build_rb(p, sc, T2, level + 1, cutoff);
-    sc.ops.push_back(Op{Op::SCATTER, i2, 0});
+    if (i2 >= 0) sc.ops.push_back(Op{Op::SCATTER, i2, 0});
 }
 
+static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb, size_t* smem,
+                                            bool whole_grid = false);
+
 static int64_t auto_cutoff(const stencil_plan_s* p) {
-    if (p->cutoff >= 2) return p->cutoff;
     // the loop's cost per leaf grows with T_b^2 while each recursion level costs
     // about three frame-sized FFT solves
-    if (p->ndim == 1) return 256;
-    if (p->ndim == 2) return 32;
-    return 8;
+    int64_t want = p->ndim == 1 ? 256 : p->ndim == 2 ? 32 : 8;
+    if (p->cutoff >= 2) want = p->cutoff;
+    // every base-case tile (output box plus the T_b-step halo) must fit in shared
+    // memory: lower the cutoff until the largest leaf (T_b = cutoff - 1) fits
+    while (want > 2) {
+        size_t smem = 0;
+        make_base_tiles(p, want - 1, &smem);
+        if (smem <= (size_t)kSmemBudget) break;
+        --want;
+    }
+    return want;
 }
 
 // byte offsets of each batch in its level's buffers; returns the totals
@@ -655,7 +836,8 @@ static cudaError_t ensure_level(AperiodicState* st, int level, size_t sb, size_t
 }
 
 // Output tiles of the frame dist <= w for the base case.
-static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb, size_t* smem) {
+static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb, size_t* smem,
+                                            bool whole_grid) {
     const int d = p->ndim;
     const int w = (int)(p->radius * Tb);
     const int h = w;
@@ -664,7 +846,7 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
     // regions: bands per face, earlier axes' bands excluded
     struct Region { int lo[3], hi[3]; int normal; };
     std::vector<Region> regions;
-    bool whole = false;
+    bool whole = whole_grid;
     for (int a = 0; a < d; ++a)
         if (2 * (int64_t)w >= p->dims[a]) whole = true;
     if (whole) {
@@ -726,12 +908,12 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
                     tiles.push_back(t);
                 }
     }
-    if (d == 2) {
-        // k_base_2d: (extent + 2 RAD) per axis, two buffers
+    {
+        // k_base_1d/2d/3d: (extent + 2 RAD) per axis, two buffers
         size_t m = 0;
         for (const BaseTile& t : tiles) {
             size_t v = 1;
-            for (int a = 0; a < 2; ++a) {
+            for (int a = 0; a < d; ++a) {
                 const int lo = std::max(t.lo[a] - h, 0);
                 const int hi = std::min<int>(t.hi[a] + h, (int)p->dims[a]);
                 v *= (size_t)(hi - lo + 2 * p->radius);
@@ -739,42 +921,39 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
             m = std::max(m, v);
         }
         *smem = 2 * m * p->elem;
-    } else {
-        *smem = 2 * max_vol * p->elem;
     }
+    (void)max_vol;
     return tiles;
 }
 
 template <typename R>
 static cudaError_t launch_base(stencil_plan_s* p, const BaseSet& bs, R* X, R* Y, int64_t Tb,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool whole = false) {
     BaseParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.ndim = p->ndim;
     for (int a = 0; a < p->ndim; ++a) bp.gdims[a] = (int)p->dims[a];
     bp.Tb = (int)Tb;
-    bp.wout = (int)(p->radius * Tb);
-    for (int i = 0; i < p->nweights; ++i) bp.w[i] = p->weights[i];
+    bp.wout = whole ? 0x3fffffff : (int)(p->radius * Tb);
+    for (int i = 0; i < p->nweights; ++i) {
+        bp.w[i] = p->weights[i];
+        bp.wf[i] = (float)p->weights[i];
+    }
     const BaseTile* tiles = static_cast<const BaseTile*>(bs.tiles);
     cudaError_t err = cudaSuccess;
     p->prof.begin(PASS_BASE_LOOP, s);
     switch (p->radius) {
 #define SFFT_BASE_CASE(RADV)                                                                  \
     case RADV:                                                                                \
-        if (p->ndim == 2) {                                                                   \
+        {                                                                                     \
+            auto kern = p->ndim == 1 ? k_base_1d<R, RADV>                                     \
+                                     : p->ndim == 2 ? k_base_2d<R, RADV> : k_base_3d<R, RADV>; \
             if (bs.smem > 48 * 1024)                                                          \
-                err = smem_optin(reinterpret_cast<const void*>(k_base_2d<R, RADV>), bs.smem); \
+                err = smem_optin(reinterpret_cast<const void*>(kern), bs.smem);              \
             if (err == cudaSuccess) {                                                         \
-                k_base_2d<R, RADV><<<bs.count, 256, bs.smem, s>>>(X, Y, tiles, bp);          \
+                kern<<<bs.count, 256, bs.smem, s>>>(X, Y, tiles, bp);                         \
                 err = cudaGetLastError();                                                     \
             }                                                                                 \
-            break;                                                                            \
-        }                                                                                     \
-        if (bs.smem > 48 * 1024)                                                              \
-            err = smem_optin(reinterpret_cast<const void*>(k_base_tiles<R, RADV>), bs.smem);  \
-        if (err == cudaSuccess) {                                                             \
-            k_base_tiles<R, RADV><<<bs.count, 256, bs.smem, s>>>(X, Y, tiles, bp);            \
-            err = cudaGetLastError();                                                         \
         }                                                                                     \
         break;
         SFFT_BASE_CASE(0)
@@ -822,6 +1001,110 @@ static void assign_tables(const stencil_plan_s* p, Schedule& sc) {
             }
 }
 
+// T single steps of the loop over the whole grid (3-D), X -> Y -> X ...
+template <typename R>
+static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaStream_t s) {
+    BaseParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.ndim = p->ndim;
+    for (int a = 0; a < p->ndim; ++a) bp.gdims[a] = (int)p->dims[a];
+    for (int i = 0; i < p->nweights; ++i) {
+        bp.w[i] = p->weights[i];
+        bp.wf[i] = (float)p->weights[i];
+    }
+    const int blocks = grid_blocks(p->n_cells);
+    cudaError_t err = cudaSuccess;
+    R* a = X;
+    R* b = Y;
+    p->prof.begin(PASS_BASE_LOOP, s);
+    for (int64_t t = 0; t < T && err == cudaSuccess; ++t) {
+        switch (p->radius) {
+            case 1: k_step_3d<R, 1><<<blocks, 256, 0, s>>>(a, b, bp); break;
+            case 2: k_step_3d<R, 2><<<blocks, 256, 0, s>>>(a, b, bp); break;
+            case 3: k_step_3d<R, 3><<<blocks, 256, 0, s>>>(a, b, bp); break;
+            default: k_step_3d<R, 0><<<blocks, 256, 0, s>>>(a, b, bp); break;
+        }
+        err = cudaGetLastError();
+        R* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    p->prof.end(s);
+    if (err == cudaSuccess && a != X)
+        err = cudaMemcpyAsync(X, a, (size_t)p->n_cells * p->elem, cudaMemcpyDeviceToDevice, s);
+    return err;
+}
+
+// Cost estimates (seconds) that decide between RecursiveBoundary and the
+// plain loop for a zero-Dirichlet solve; the constants are per-cell costs
+// measured on GB300 for FP32 (FFT passes plus copies; one stencil point of the
+// blocked loop) and the cost of one launch.
+static double fft_cell_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 8.0) * 2.0e-11; }
+static double loop_point_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 2.0) * 0.7e-12; }
+constexpr double kLaunchS = 4e-6;
+
+static double stencil_points(const stencil_plan_s* p) { return (double)p->nweights; }
+
+static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t T) {
+    double c = 0.0;
+    int64_t maxdist = p->dims[0] / 2;
+    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
+    if (p->radius * T < maxdist) c += (double)p->n_cells * fft_cell_s(p);   // interior solve
+    for (const Step& st : sc.steps)
+        for (const Batch& b : st.batches)
+            c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + 6 * kLaunchS;
+    for (const Op& op : sc.ops) {
+        if (op.kind != Op::BASE) continue;
+        size_t smem = 0;
+        const std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &smem);
+        double cells = 0.0;
+        for (const BaseTile& t : tiles) {
+            double v = 1.0;
+            for (int a = 0; a < p->ndim; ++a)
+                v *= (double)(std::min<int64_t>(t.hi[a] + p->radius * op.T, p->dims[a]) -
+                              std::max<int64_t>(t.lo[a] - p->radius * op.T, 0));
+            cells += v;
+        }
+        c += cells * (double)op.T * stencil_points(p) * loop_point_s(p) + 2 * kLaunchS;
+    }
+    return c;
+}
+
+// The plain loop as a schedule: whole-grid blocked tiles of Tc steps (1-D,
+// 2-D) or single steps (3-D); returns its estimated cost.
+static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
+    sc.loop = true;
+    if (p->ndim == 3) {
+        sc.ops.push_back(Op{Op::STEP, -1, T});
+        return (double)p->n_cells * (double)T * stencil_points(p) * loop_point_s(p) * 3.0 +
+               (double)T * kLaunchS;
+    }
+    double best = -1.0;
+    int64_t best_tc = 1;
+    for (int64_t tc = 1; tc <= std::min<int64_t>(T, p->ndim == 1 ? 256 : 32); tc *= 2) {
+        size_t smem = 0;
+        const std::vector<BaseTile> tiles = make_base_tiles(p, tc, &smem, true);
+        if (smem > (size_t)kSmemBudget) break;
+        double cells = 0.0;
+        for (const BaseTile& t : tiles) {
+            double v = 1.0;
+            for (int a = 0; a < p->ndim; ++a)
+                v *= (double)(std::min<int64_t>(t.hi[a] + p->radius * tc, p->dims[a]) -
+                              std::max<int64_t>(t.lo[a] - p->radius * tc, 0));
+            cells += v;
+        }
+        const double cost = cells * (double)T * stencil_points(p) * loop_point_s(p) +
+                            (double)(T / tc + 1) * 2 * kLaunchS;
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_tc = tc;
+        }
+    }
+    for (int64_t done = 0; done < T; done += best_tc)
+        sc.ops.push_back(Op{Op::LOOP, -1, std::min<int64_t>(best_tc, T - done)});
+    return best;
+}
+
 static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
     if (!p->ap) p->ap = new AperiodicState();
     AperiodicState* st = p->ap;
@@ -845,6 +1128,13 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
     if (it == st->schedules.end()) {
         Schedule sc;
         build_rb(p, sc, T, 0, auto_cutoff(p));
+        if (p->cutoff == 0) {
+            // automatic mode: the plain loop when it is the cheaper schedule (a
+            // boundary region that spans the whole grid gains nothing from FFTs)
+            Schedule loop;
+            const double c_loop = build_loop(p, loop, T);
+            if (c_loop < schedule_cost(p, sc, T)) sc = std::move(loop);
+        }
         assign_tables(p, sc);
         for (VTable& v : sc.tables) {
             const size_t vb = periodic_workspace_bytes(p->ndim, v.bdims, p->precision);
@@ -862,9 +1152,11 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
             if (err != cudaSuccess) return err;
         }
         for (const Op& op : sc.ops) {
-            if (op.kind != Op::BASE || st->base.count(op.T)) continue;
+            if (op.kind != Op::BASE && op.kind != Op::LOOP) continue;
+            const int64_t key = 2 * op.T + (op.kind == Op::LOOP ? 1 : 0);
+            if (st->base.count(key)) continue;
             BaseSet bs;
-            std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &bs.smem);
+            std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &bs.smem, op.kind == Op::LOOP);
             bs.count = (int)tiles.size();
             if (bs.smem > (size_t)kSmemBudget) return cudaErrorInvalidValue;
             err = cudaMalloc(&bs.tiles, sizeof(BaseTile) * std::max<size_t>(1, tiles.size()));
@@ -876,7 +1168,7 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
                                   cudaMemcpyHostToDevice, cudaStreamPerThread);
             if (err == cudaSuccess) err = cudaStreamSynchronize(cudaStreamPerThread);
             if (err != cudaSuccess) return err;
-            st->base[op.T] = bs;
+            st->base[key] = bs;
         }
         it = st->schedules.emplace(T, std::move(sc)).first;
     }
@@ -919,9 +1211,15 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
         if (branches && (err = cudaEventRecord(st->int_done, is)) != cudaSuccess) return err;
     }
     for (const Op& op : sc.ops) {
-        if (op.kind == Op::BASE) {
-            auto it = st->base.find(op.T);
-            err = launch_base<R>(p, it->second, X, static_cast<R*>(st->Y), op.T, main);
+        if (op.kind == Op::BASE || op.kind == Op::LOOP) {
+            auto it = st->base.find(2 * op.T + (op.kind == Op::LOOP ? 1 : 0));
+            err = launch_base<R>(p, it->second, X, static_cast<R*>(st->Y), op.T, main,
+                                 op.kind == Op::LOOP);
+            if (err != cudaSuccess) return err;
+            continue;
+        }
+        if (op.kind == Op::STEP) {
+            err = launch_steps<R>(p, X, static_cast<R*>(st->Y), op.T, main);
             if (err != cudaSuccess) return err;
             continue;
         }
@@ -1011,10 +1309,10 @@ static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStr
                                  p->E32, p->status, s);
     int64_t maxdist = p->dims[0] / 2;
     for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
-    const bool interior = sigma * T < maxdist;
     Schedule* sc = nullptr;
     cudaError_t err = prepare(p, T, &sc);
     if (err != cudaSuccess) return err;
+    const bool interior = !sc->loop && sigma * T < maxdist;
     AperiodicState* st = p->ap;
     if (interior && !st->Z) {
         err = cudaMalloc(&st->Z, (size_t)p->n_cells * p->elem);
@@ -1115,10 +1413,24 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
         if (dims[a] < 4 || ilog2_exact(dims[a]) < 0) return -1;
         p.dims[a] = dims[a];
     }
+    p.n_cells = 1;
+    for (int a = 0; a < ndim; ++a) p.n_cells *= dims[a];
+    p.nweights = 1;
+    for (int a = 0; a < ndim; ++a) p.nweights *= 2 * radius + 1;
     Schedule sc;
     build_rb(&p, sc, T, 0, auto_cutoff(&p));
+    if (cutoff == 0) {
+        Schedule loop;
+        const double c_loop = build_loop(&p, loop, T);
+        if (c_loop < schedule_cost(&p, sc, T)) sc = std::move(loop);
+    }
     std::vector<int64_t> v;
     for (const Op& op : sc.ops) {
+        if (op.kind == Op::LOOP || op.kind == Op::STEP) {
+            v.push_back(op.kind == Op::LOOP ? 4 : 5);
+            v.push_back(op.T);
+            continue;
+        }
         if (op.kind == Op::BASE) {
             size_t smem = 0;
             std::vector<BaseTile> tiles = make_base_tiles(&p, op.T, &smem);

@@ -36,7 +36,7 @@ def err_rel(got, ref, a0):
 CASES = [
     ((64,), 1), ((256,), 2), ((4096,), 1),
     ((32, 32), 1), ((64, 128), 1), ((128, 64), 2), ((256, 256), 1),
-    ((16, 16, 16), 1), ((32, 16, 64), 1),
+    ((16, 16, 16), 1), ((32, 16, 64), 1), ((16, 16, 32), 2),
 ]
 
 

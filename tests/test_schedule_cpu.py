@@ -53,6 +53,9 @@ def decode(v):
         elif kind == 2:
             ops.append(("scatter", v[i + 1]))
             i += 2
+        elif kind in (4, 5):
+            ops.append(("loop", v[i + 1]))
+            i += 2
         elif kind == 3:
             Tb, n = v[i + 1], v[i + 2]
             i += 3
@@ -83,10 +86,14 @@ def emulate(a0, w, T, ops):
     dist = oracle.boundary_distance(dims)
     X = a0.copy()
     maxdist = min(l // 2 for l in dims)
-    Z = oracle.stencil_fft_periodic(a0, w, T) if r * T < maxdist else None
+    loop = any(op[0] == "loop" for op in ops)
+    Z = oracle.stencil_fft_periodic(a0, w, T) if r * T < maxdist and not loop else None
     stash = {}
     grids = np.meshgrid(*[np.arange(l) for l in dims], indexing="ij")
     for op in ops:
+        if op[0] == "loop":
+            X = oracle.stencil_loop(X, w, op[1], "dirichlet")
+            continue
         if op[0] == "solve":
             _, step, Tk, level, strips = op
             out = []
@@ -188,3 +195,24 @@ def test_schedule_rejects_bad_arguments(lib):
     assert lib.stencil_debug_schedule(1, d, 1, 5, 1, None, 0) == -1
     d12 = (ctypes.c_int64 * 1)(12)
     assert lib.stencil_debug_schedule(1, d12, 1, 5, 0, None, 0) == -1
+
+
+def test_auto_mode_picks_the_loop_when_everything_is_boundary(lib):
+    # sigma T far beyond the grid: every cell feels the boundary, FFTs cannot help
+    ops = decode(fetch_schedule(lib, (64, 64), 2, 5000, 0))
+    assert ops and all(o[0] == "loop" for o in ops) and sum(o[1] for o in ops) == 5000
+    ops = decode(fetch_schedule(lib, (16, 16, 16), 1, 300, 0))
+    assert ops == [("loop", 300)]
+    # the benchmark regime stays recursive
+    ops = decode(fetch_schedule(lib, (8192, 8192), 1, 4096, 0))
+    assert any(o[0] == "solve" for o in ops)
+
+
+@pytest.mark.parametrize("dims,r,T", [((32, 32), 2, 300), ((16, 16, 16), 1, 40), ((128,), 1, 900)])
+def test_auto_loop_schedule_reproduces_dirichlet_loop(lib, dims, r, T):
+    w = wl.weights_random_box(len(dims), r, 5)
+    a0 = wl.grid_uniform(dims, 6)
+    ops = decode(fetch_schedule(lib, dims, r, T, 0))
+    got = emulate(a0, w, T, ops)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    assert np.max(np.abs(got - ref)) < 1e-11
