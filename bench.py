@@ -31,6 +31,35 @@ UNIT = "point-updates/s"
 WORKLOAD = "star5_2d_periodic_4096x4096_T10000"
 
 
+# Kernel sources whose hash keys the DRAM traffic recorded under profiles/: a
+# traffic figure is reported only while the kernels are the ones it was taken on.
+KERNEL_SOURCES = ["periodic_kernels.cuh", "fft_ct.cuh", "fft_reg.cuh", "fft_common.cuh",
+                  "symbol.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_star5_2d_4096_fp32.json")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2105_06676_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(kind: str):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of
+    kernel `kind`, or None when not recorded for the current kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch", {}).get(kind)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -259,6 +288,8 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--no-dirichlet", action="store_true",
+                    help="skip the zero-Dirichlet secondary measurement (short profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -298,13 +329,20 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region: FP32 path, per-kernel events on the launching stream
+    # ---- timed region: FP32 path, per-kernel events on the launching stream.
+    # One untimed solve first, so that module loading and table setup are not
+    # in the per-kernel averages.
+    plan32.run(g32, T)
+    plan64.run(g64, T)
+    g32.copy_(pristine32)
+    g64.copy_(pristine64)
+    torch.cuda.synchronize()
     plan32.profile(True)
     barrier()
     with ClockSampler(local) as clk:
         times32 = time_solve(plan32, g32, pristine32, flush, args.steps, args.warmup, T)
     barrier()
-    prof = plan32.profile_read()          # includes warm-up launches; split below
+    prof = plan32.profile_read()          # warm-up and timed launches
     plan32.profile(False)
     ms32 = sum(times32) / len(times32)
     if world > 1:
@@ -319,16 +357,20 @@ def main():
     ms64 = sum(times64) / len(times64)
 
     # ---- zero-Dirichlet path (secondary): 8192^2 9-point box, T = 4096, FP32
-    wd = wl.box2d_8192_dirichlet()
-    ad = wd.grid()
-    pland = StencilPlan(wd.dims, wd.weights, "dirichlet", "fp32")
-    pris_d = torch.tensor(ad, dtype=torch.float32, device="cuda")
-    gd = pris_d.clone()
-    times_d = time_solve(pland, gd, pris_d, flush, 2, 1, wd.T)
-    ms_d = sum(times_d) / len(times_d)
-    assert pland.status() == 0
-    del gd, pris_d
-    pland.close()
+    dirichlet = None
+    if not args.no_dirichlet:
+        wd = wl.box2d_8192_dirichlet()
+        ad = wd.grid()
+        pland = StencilPlan(wd.dims, wd.weights, "dirichlet", "fp32")
+        pris_d = torch.tensor(ad, dtype=torch.float32, device="cuda")
+        gd = pris_d.clone()
+        times_d = time_solve(pland, gd, pris_d, flush, 2, 1, wd.T)
+        ms_d = sum(times_d) / len(times_d)
+        assert pland.status() == 0
+        del gd, pris_d
+        pland.close()
+        dirichlet = {"workload": wd.name, "value": world * wd.n_cells * wd.T / (ms_d * 1e-3),
+                     "ms_per_step": ms_d}
 
     # ---- serving: mixed stream through the continuous-batching server
     serving = serve_mixed_stream(args.serve_requests) if args.serve_requests > 0 else None
@@ -357,13 +399,7 @@ def main():
     algo = {"rows_r2c": grid_bytes + half_bytes, "cols_fused": 2 * half_bytes,
             "rows_c2r": half_bytes + grid_bytes}
     achieved = algo[dominant] / (avg_ms[dominant] * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic_star5_2d_4096_fp32.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get(dominant)
-        except Exception:
-            traffic = None
+    traffic = kernel_traffic(dominant)
     step_kernel_launches = sum(launches.values()) / (args.steps + args.warmup)
 
     cpu = None
@@ -384,8 +420,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed (512 MiB write) between timed steps; grid restored outside the events"},
             "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64},
-            "dirichlet_path": {"workload": wd.name, "value": world * wd.n_cells * wd.T / (ms_d * 1e-3),
-                               "ms_per_step": ms_d},
+            "dirichlet_path": dirichlet,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": grid_bytes,
                     "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,

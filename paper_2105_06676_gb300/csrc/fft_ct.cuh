@@ -22,6 +22,41 @@ struct PadLayout {
     static __host__ __device__ constexpr int off(int p) { return (p << SL) + (p >> S); }
 };
 
+// Exchange through shared memory: thread j writes v[r] at element wbase + wstep(r)
+// and reads back elements j + q s into v[s].
+template <int SL, int S, int LOG2N, typename C>
+__device__ __forceinline__ void ct_read(C* v, const C* sm, int j) {
+    using L = PadLayout<SL, S>;
+    constexpr int q = (1 << LOG2N) >> 4;
+    const C* rd = sm + L::off(j);
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = rd[L::off(q * s)];
+}
+
+// Radix-16 stages from sub-transform length 2^NSL up to n.
+template <int DIR, int LOG2N, int NSL, int SL, int S, typename C>
+__device__ __forceinline__ void ct_stages(C* v, C* sm, int j, const C* __restrict__ tw,
+                                          int twn_log2) {
+    if constexpr (NSL < LOG2N) {
+        using L = PadLayout<SL, S>;
+        constexpr int Ns = 1 << NSL;
+        const int k = j & (Ns - 1);
+        // twiddle by w_{16 Ns}^{k s}, then the radix-16 butterfly
+        reg_twiddle<DIR>(v, k, twn_log2 - NSL - 4, tw);
+        dft_reg<16, DIR>(v);
+        if constexpr (NSL + 4 < LOG2N) {
+            // output r of butterfly j goes to (j - k) 16 + k + Ns r
+            C* w = sm + L::off((j - k) * 16 + k);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[L::off(Ns * r)] = v[r];
+            __syncthreads();
+            ct_read<SL, S, LOG2N>(v, sm, j);
+            __syncthreads();
+            ct_stages<DIR, LOG2N, NSL + 4, SL, S>(v, sm, j, tw, twn_log2);
+        }
+    }
+}
+
 template <int DIR, int LOG2N, int SL, int S, typename C>
 __device__ __forceinline__ void ct_fft(C* v, C* sm, int j, const C* __restrict__ tw, int twn_log2) {
     using L = PadLayout<SL, S>;
@@ -32,47 +67,16 @@ __device__ __forceinline__ void ct_fft(C* v, C* sm, int j, const C* __restrict__
     constexpr int G = 16 / R0;
     reg_first_stage<R0, DIR>(v);
     if constexpr (R0 < n) {
-        // exchange after the first stage: output r of butterfly j + q t at (j + q t) R0 + r
-        {
-            C* w = sm + L::off(j * R0);
+        // output r of first-stage butterfly j + q t goes to (j + q t) R0 + r
+        C* w = sm + L::off(j * R0);
 #pragma unroll
-            for (int t = 0; t < G; ++t)
+        for (int t = 0; t < G; ++t)
 #pragma unroll
-                for (int r = 0; r < R0; ++r) w[L::off(q * t * R0 + r)] = v[t * R0 + r];
-        }
+            for (int r = 0; r < R0; ++r) w[L::off(q * t * R0 + r)] = v[t * R0 + r];
         __syncthreads();
-        {
-            const C* rd = sm + L::off(j);
-#pragma unroll
-            for (int s = 0; s < 16; ++s) v[s] = rd[L::off(q * s)];
-        }
+        ct_read<SL, S, LOG2N>(v, sm, j);
         __syncthreads();
-#pragma unroll
-        for (int Ns = R0; Ns < n; Ns <<= 4) {
-            constexpr int dummy = 0;
-            (void)dummy;
-            const int k = j & (Ns - 1);
-            // twiddle by w_{16 Ns}^{k s}
-            int ns_log2 = 0;
-            while ((1 << ns_log2) < Ns) ++ns_log2;
-            reg_twiddle<DIR>(v, k, twn_log2 - ns_log2 - 4, tw);
-            dft_reg<16, DIR>(v);
-            if (Ns * 16 < n) {
-                // exchange: output r of butterfly j at (j - k) 16 + k + Ns r
-                {
-                    C* w = sm + L::off((j - k) * 16 + k);
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) w[L::off(Ns * r)] = v[r];
-                }
-                __syncthreads();
-                {
-                    const C* rd = sm + L::off(j);
-#pragma unroll
-                    for (int s = 0; s < 16; ++s) v[s] = rd[L::off(q * s)];
-                }
-                __syncthreads();
-            }
-        }
+        ct_stages<DIR, LOG2N, r0log, SL, S>(v, sm, j, tw, twn_log2);
     }
 }
 

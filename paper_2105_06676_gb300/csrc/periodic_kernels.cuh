@@ -22,7 +22,9 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
+#include "fft_ct.cuh"
 #include "fft_reg.cuh"
 #include "internal.h"
 
@@ -31,6 +33,27 @@ namespace sfft {
 template <typename R> struct MaxT;
 template <> struct MaxT<float> { static constexpr int v = kMaxThreadsF32; };
 template <> struct MaxT<double> { static constexpr int v = kMaxThreadsF64; };
+
+// Resident CTAs per SM the column kernels are compiled for: FP32 CTAs below
+// 1024 threads keep 64 registers per thread so that 2048 / MAXT CTAs fit.
+template <typename R, int MAXT>
+struct ColMinBlocks {
+    static constexpr int v = (sizeof(R) == 4 && MAXT < 1024) ? 1024 / MAXT : 1;
+};
+
+// FFT of one sequence: compile-time length when LOG2N > 0, else runtime.
+template <int DIR, int LOG2N, typename C>
+__device__ __forceinline__ void seq_fft(C* v, const SeqView<C>& sm, int j, int log2n,
+                                        const C* __restrict__ tw, int twn_log2) {
+    if constexpr (LOG2N > 0) ct_fft<DIR, LOG2N, 0, 5>(v, sm.base, j, tw, twn_log2);
+    else reg_fft<DIR>(v, sm, j, log2n, tw, twn_log2);
+}
+template <int DIR, int LOG2N, int CL, typename C>
+__device__ __forceinline__ void col_fft(C* v, const ColView<C>& sm, int j, int log2n,
+                                        const C* __restrict__ tw, int twn_log2) {
+    if constexpr (LOG2N > 0) ct_fft<DIR, LOG2N, CL, 4 - CL>(v, sm.base + sm.c, j, tw, twn_log2);
+    else reg_fft<DIR>(v, sm, j, log2n, tw, twn_log2);
+}
 
 __device__ __forceinline__ bool finite2(float2 v) { return isfinite(v.x) && isfinite(v.y); }
 __device__ __forceinline__ bool finite2(double2 v) { return isfinite(v.x) && isfinite(v.y); }
@@ -303,7 +326,7 @@ __global__ void k_vtable(typename CxOf<R>::T* __restrict__ V, const __grid_const
 // sequence, 16 elements per thread, two shared-memory exchanges per 4096-point
 // transform instead of a shared-memory round trip per stage
 // ---------------------------------------------------------------------------
-template <typename R, int RAD, int MAXT>
+template <typename R, int RAD, int MAXT, int LOG2N>
 __global__ void __launch_bounds__(MAXT)
 k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
                const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
@@ -312,6 +335,7 @@ k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
+    if constexpr (LOG2N > 0) n_log2 = LOG2N;
     const int n = 1 << n_log2, q = n >> 4;
     const int ss = seq_stride(n);
     const int c = threadIdx.x / q, j = threadIdx.x - c * q;
@@ -322,7 +346,7 @@ k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
     C v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? rowp[j + q * s] : C{0, 0};
-    reg_fft<-1>(v, sm, j, n_log2, tw, twn_log2);
+    seq_fft<-1, LOG2N>(v, sm, j, n_log2, tw, twn_log2);
     // real-input split: X[k] from Z[k] and Z[n-k]
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
@@ -369,7 +393,7 @@ k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
         v[r] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
     }
     __syncthreads();
-    reg_fft<+1>(v, sm, j, n_log2, tw, twn_log2);
+    seq_fft<+1, LOG2N>(v, sm, j, n_log2, tw, twn_log2);
     bool bad = false;
     if (live) {
 #pragma unroll
@@ -381,7 +405,7 @@ k_fused_1d_reg(R* __restrict__ grid, int n_log2, int nrows, int rpc,
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
 }
 
-template <typename R, int MAXT>
+template <typename R, int MAXT, int LOG2N>
 __global__ void __launch_bounds__(MAXT)
 k_rows_r2c_reg(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, long long Mp,
                int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
@@ -389,6 +413,7 @@ k_rows_r2c_reg(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, 
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
+    if constexpr (LOG2N > 0) n_log2 = LOG2N;
     const int n = 1 << n_log2, q = n >> 4;
     const int ss = seq_stride(n);
     const int c = threadIdx.x / q, j = threadIdx.x - c * q;
@@ -399,7 +424,7 @@ k_rows_r2c_reg(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, 
     C v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? __ldg(rowp + j + q * s) : C{0, 0};
-    reg_fft<-1>(v, sm, j, n_log2, tw, twn_log2);
+    seq_fft<-1, LOG2N>(v, sm, j, n_log2, tw, twn_log2);
 #pragma unroll
     for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
     __syncthreads();
@@ -417,7 +442,7 @@ k_rows_r2c_reg(const R* __restrict__ grid, typename CxOf<R>::T* __restrict__ H, 
     }
 }
 
-template <typename R, int MAXT>
+template <typename R, int MAXT, int LOG2N>
 __global__ void __launch_bounds__(MAXT)
 k_rows_c2r_reg(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, long long Mp,
                int n_log2, int nrows, int rpc, const typename CxOf<R>::T* __restrict__ tw,
@@ -425,6 +450,7 @@ k_rows_c2r_reg(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, 
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
+    if constexpr (LOG2N > 0) n_log2 = LOG2N;
     const int n = 1 << n_log2, q = n >> 4;
     const int ss = seq_stride(n);
     const int c = threadIdx.x / q, j = threadIdx.x - c * q;
@@ -442,7 +468,7 @@ k_rows_c2r_reg(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, 
         const C wk = tw[k << sh];
         v[s] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
     }
-    reg_fft<+1>(v, sm, j, n_log2, tw, twn_log2);
+    seq_fft<+1, LOG2N>(v, sm, j, n_log2, tw, twn_log2);
     bool bad = false;
     if (live) {
         C* rowp = reinterpret_cast<C*>(grid) + row * n;
@@ -455,32 +481,34 @@ k_rows_c2r_reg(const typename CxOf<R>::T* __restrict__ H, R* __restrict__ grid, 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
 }
 
-template <typename R, int DIR, int MAXT>
-__global__ void __launch_bounds__(MAXT)
+template <typename R, int DIR, int MAXT, int LOG2N, int CL>
+__global__ void __launch_bounds__(MAXT, ColMinBlocks<R, MAXT>::v)
 k_cols_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
            const typename CxOf<R>::T* __restrict__ tw, int twn_log2) {
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
-    const int n = 1 << g.log2n, q = n >> 4;
-    const int cols = 1 << g.cols_log2;
-    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> g.cols_log2;
-    const int i0 = blockIdx.x << g.cols_log2;
+    const int log2n = LOG2N > 0 ? LOG2N : g.log2n;
+    const int cl = LOG2N > 0 ? CL : g.cols_log2;
+    const int n = 1 << log2n, q = n >> 4;
+    const int cols = 1 << cl;
+    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> cl;
+    const int i0 = blockIdx.x << cl;
     const bool live = i0 + c < g.inner_valid;
-    const ColView<C> sm{small, c, g.cols_log2};
+    const ColView<C> sm{small, c, cl};
     C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
     C v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : C{0, 0};
-    reg_fft<DIR>(v, sm, j, g.log2n, tw, twn_log2);
+    col_fft<DIR, LOG2N, CL>(v, sm, j, log2n, tw, twn_log2);
     if (live) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
     }
 }
 
-template <typename R, int RAD, int MAXT>
-__global__ void __launch_bounds__(MAXT)
+template <typename R, int RAD, int MAXT, int LOG2N, int CL>
+__global__ void __launch_bounds__(MAXT, ColMinBlocks<R, MAXT>::v)
 k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ ColGeom g,
                  const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
                  const __grid_constant__ SymbolSet ps) {
@@ -488,17 +516,19 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
     using C = typename CxOf<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* small = reinterpret_cast<C*>(smraw);
-    const int n = 1 << g.log2n, q = n >> 4;
-    const int cols = 1 << g.cols_log2;
-    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> g.cols_log2;
-    const int i0 = blockIdx.x << g.cols_log2;
+    const int log2n = LOG2N > 0 ? LOG2N : g.log2n;
+    const int cl = LOG2N > 0 ? CL : g.cols_log2;
+    const int n = 1 << log2n, q = n >> 4;
+    const int cols = 1 << cl;
+    const int c = threadIdx.x & (cols - 1), j = threadIdx.x >> cl;
+    const int i0 = blockIdx.x << cl;
     const bool live = i0 + c < g.inner_valid;
-    const ColView<C> sm{small, c, g.cols_log2};
+    const ColView<C> sm{small, c, cl};
     C* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
     C v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : C{0, 0};
-    reg_fft<-1>(v, sm, j, g.log2n, tw, twn_log2);
+    col_fft<-1, LOG2N, CL>(v, sm, j, log2n, tw, twn_log2);
     int k[3];
     if (p.ndim == 2) {
         k[1] = i0 + c;
@@ -522,7 +552,7 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
         apply_multiplier<RAD>(v, sm, j, q, p, cs, k[1], k[2]);
     }
     __syncthreads();
-    reg_fft<+1>(v, sm, j, g.log2n, tw, twn_log2);
+    col_fft<+1, LOG2N, CL>(v, sm, j, log2n, tw, twn_log2);
     if (live) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
@@ -556,8 +586,10 @@ static int reg_rows_per_cta(int n_log2) {
     return rpc;
 }
 
-// Threads per CTA of the register column kernels (512 or 1024; the
-// environment variable STENCILFFT_COL_THREADS overrides the default of 1024).
+// Threads per CTA of the FP32 register column kernels (512 or 1024; the
+// environment variable STENCILFFT_COL_THREADS overrides the default of 1024,
+// which measured fastest: 4 columns of a 4096-point transform per CTA read
+// 32-byte row segments, full sectors).
 static int col_threads_cap() {
     static int cap = [] {
         const char* e = std::getenv("STENCILFFT_COL_THREADS");
@@ -565,6 +597,21 @@ static int col_threads_cap() {
         return v == 512 ? 512 : 1024;
     }();
     return cap;
+}
+
+// Transform lengths (log2) with compile-time specialised register kernels;
+// other lengths run the runtime-length kernels (LOG2N = 0).
+constexpr int kCtLo = 8, kCtHi = 13;
+
+// Calls f(std::integral_constant<int, L>) with L = l if LO <= l <= HI, else L = 0.
+template <int LO, int HI, typename F>
+static cudaError_t with_log2n(int l, F&& f) {
+    if constexpr (LO > HI) {
+        return f(std::integral_constant<int, 0>{});
+    } else {
+        if (l == LO) return f(std::integral_constant<int, LO>{});
+        return with_log2n<LO + 1, HI>(l, f);
+    }
 }
 
 template <typename R, int RAD, int MAXT>
@@ -576,10 +623,10 @@ static cudaError_t launch_fused_1d_reg_t(R* grid, int n_log2, int nrows, const v
     const int rpc = reg_rows_per_cta(n_log2);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
     const int threads = rpc * (n >> 4);
-    cudaError_t err = set_smem(k_fused_1d_reg<R, RAD, MAXT>, smem);
+    cudaError_t err = set_smem(k_fused_1d_reg<R, RAD, MAXT, 0>, smem);
     if (err != cudaSuccess) return err;
     const int blocks = (nrows + rpc - 1) / rpc;
-    k_fused_1d_reg<R, RAD, MAXT><<<blocks, threads, smem, s>>>(
+    k_fused_1d_reg<R, RAD, MAXT, 0><<<blocks, threads, smem, s>>>(
         grid, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2, p, status, rt);
     return cudaGetLastError();
 }
@@ -602,11 +649,15 @@ static cudaError_t launch_rows_r2c_reg(const R* grid, void* H, long long Mp, int
     const int n = 1 << n_log2;
     const int rpc = reg_rows_per_cta(n_log2);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
-    cudaError_t err = set_smem(k_rows_r2c_reg<R, MAXT>, smem);
-    if (err != cudaSuccess) return err;
-    k_rows_r2c_reg<R, MAXT><<<(nrows + rpc - 1) / rpc, rpc * (n >> 4), smem, s>>>(
-        grid, static_cast<C*>(H), Mp, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2);
-    return cudaGetLastError();
+    const dim3 blocks((nrows + rpc - 1) / rpc), threads(rpc * (n >> 4));
+    return with_log2n<kCtLo, kCtHi>(n_log2, [&](auto tag) {
+        constexpr int L = decltype(tag)::value;
+        cudaError_t err = set_smem(k_rows_r2c_reg<R, MAXT, L>, smem);
+        if (err != cudaSuccess) return err;
+        k_rows_r2c_reg<R, MAXT, L><<<blocks, threads, smem, s>>>(
+            grid, static_cast<C*>(H), Mp, n_log2, nrows, rpc, static_cast<const C*>(tw), twn_log2);
+        return cudaGetLastError();
+    });
 }
 
 template <typename R, int MAXT>
@@ -617,22 +668,27 @@ static cudaError_t launch_rows_c2r_reg(const void* H, R* grid, long long Mp, int
     const int n = 1 << n_log2;
     const int rpc = reg_rows_per_cta(n_log2);
     const size_t smem = (size_t)rpc * seq_stride(n) * sizeof(C);
-    cudaError_t err = set_smem(k_rows_c2r_reg<R, MAXT>, smem);
-    if (err != cudaSuccess) return err;
-    k_rows_c2r_reg<R, MAXT><<<(nrows + rpc - 1) / rpc, rpc * (n >> 4), smem, s>>>(
-        static_cast<const C*>(H), grid, Mp, n_log2, nrows, rpc, static_cast<const C*>(tw),
-        twn_log2, status);
-    return cudaGetLastError();
+    const dim3 blocks((nrows + rpc - 1) / rpc), threads(rpc * (n >> 4));
+    return with_log2n<kCtLo, kCtHi>(n_log2, [&](auto tag) {
+        constexpr int L = decltype(tag)::value;
+        cudaError_t err = set_smem(k_rows_c2r_reg<R, MAXT, L>, smem);
+        if (err != cudaSuccess) return err;
+        k_rows_c2r_reg<R, MAXT, L><<<blocks, threads, smem, s>>>(
+            static_cast<const C*>(H), grid, Mp, n_log2, nrows, rpc, static_cast<const C*>(tw),
+            twn_log2, status);
+        return cudaGetLastError();
+    });
 }
 
 // column count (log2) of the register column kernels for MAXT threads per CTA
 static int reg_cols_log2(int log2n, int elem_bytes, int maxt) {
-    const int q = 1 << (log2n - 4);
-    int cl = 0;
-    while (cl < 4 && (2 << cl) * q <= maxt &&
-           (long long)colview_elems(1 << log2n, 2 << cl) * elem_bytes <= kSmemBudget)
-        ++cl;
-    return cl;
+    return ct_cols_log2(log2n, elem_bytes, maxt, kSmemBudget);
+}
+
+// The default thread cap of the column kernels for real type R.
+template <typename R>
+static int col_maxt() {
+    return sizeof(R) == 8 ? 512 : col_threads_cap();
 }
 
 template <typename R, int DIR, int MAXT>
@@ -643,37 +699,58 @@ static cudaError_t launch_cols_reg(void* H, ColGeom g, const void* tw, int twn_l
     g.cols_log2 = reg_cols_log2(g.log2n, sizeof(C), MAXT);
     const int cols = 1 << g.cols_log2;
     const size_t smem = (size_t)colview_elems(n, cols) * sizeof(C);
-    cudaError_t err = set_smem(k_cols_reg<R, DIR, MAXT>, smem);
-    if (err != cudaSuccess) return err;
-    dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
-    k_cols_reg<R, DIR, MAXT><<<grid, cols * (n >> 4), smem, s>>>(static_cast<C*>(H), g,
-                                                                  static_cast<const C*>(tw),
-                                                                  twn_log2);
-    return cudaGetLastError();
+    const dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
+    const int threads = cols * (n >> 4);
+    // compile-time lengths only at the default thread cap
+    constexpr bool ct = MAXT == (sizeof(R) == 8 ? 512 : 1024);
+    return with_log2n<kCtLo, ct ? kCtHi : 0>(g.log2n, [&](auto tag) {
+        constexpr int L = decltype(tag)::value;
+        constexpr int CL = L > 0 ? ct_cols_log2(L, sizeof(C), MAXT, kSmemBudget) : 0;
+        cudaError_t err = set_smem(k_cols_reg<R, DIR, MAXT, L, CL>, smem);
+        if (err != cudaSuccess) return err;
+        k_cols_reg<R, DIR, MAXT, L, CL><<<grid, threads, smem, s>>>(
+            static_cast<C*>(H), g, static_cast<const C*>(tw), twn_log2);
+        return cudaGetLastError();
+    });
 }
 
-template <typename R, int RAD, int MAXT>
+template <typename R, int RAD, int MAXT, int L>
 static cudaError_t launch_cols_fused_reg_t(void* H, ColGeom g, const void* tw, int twn_log2,
                                            const SymbolSet& p, cudaStream_t s) {
     using C = typename CxOf<R>::T;
     const int n = 1 << g.log2n;
     g.cols_log2 = reg_cols_log2(g.log2n, sizeof(C), MAXT);
+    constexpr int CL = L > 0 ? ct_cols_log2(L, sizeof(C), MAXT, kSmemBudget) : 0;
     const int cols = 1 << g.cols_log2;
     const size_t smem = (size_t)colview_elems(n, cols) * sizeof(C);
-    cudaError_t err = set_smem(k_cols_fused_reg<R, RAD, MAXT>, smem);
+    cudaError_t err = set_smem(k_cols_fused_reg<R, RAD, MAXT, L, CL>, smem);
     if (err != cudaSuccess) return err;
     dim3 grid((g.inner_valid + cols - 1) / cols, g.mid, g.outer);
-    k_cols_fused_reg<R, RAD, MAXT><<<grid, cols * (n >> 4), smem, s>>>(
+    k_cols_fused_reg<R, RAD, MAXT, L, CL><<<grid, cols * (n >> 4), smem, s>>>(
         static_cast<C*>(H), g, static_cast<const C*>(tw), twn_log2, p);
     return cudaGetLastError();
+}
+
+// Stencil radii 1 and 2 at the default thread cap get compile-time lengths.
+template <typename R, int RAD, int MAXT>
+static cudaError_t launch_cols_fused_reg_m(void* H, const ColGeom& g, const void* tw,
+                                           int twn_log2, const SymbolSet& p, cudaStream_t s) {
+    constexpr bool ct = (RAD == 1 || RAD == 2) && MAXT == (sizeof(R) == 8 ? 512 : 1024);
+    if constexpr (ct) {
+        return with_log2n<kCtLo, kCtHi>(g.log2n, [&](auto tag) {
+            return launch_cols_fused_reg_t<R, RAD, MAXT, decltype(tag)::value>(H, g, tw, twn_log2,
+                                                                                p, s);
+        });
+    } else {
+        return launch_cols_fused_reg_t<R, RAD, MAXT, 0>(H, g, tw, twn_log2, p, s);
+    }
 }
 
 template <typename R, int RAD>
 static cudaError_t launch_cols_fused_reg_r(void* H, const ColGeom& g, const void* tw,
                                            int twn_log2, const SymbolSet& p, cudaStream_t s) {
-    if (sizeof(R) == 8 || col_threads_cap() == 512)
-        return launch_cols_fused_reg_t<R, RAD, 512>(H, g, tw, twn_log2, p, s);
-    return launch_cols_fused_reg_t<R, RAD, 1024>(H, g, tw, twn_log2, p, s);
+    if (col_maxt<R>() == 512) return launch_cols_fused_reg_m<R, RAD, 512>(H, g, tw, twn_log2, p, s);
+    return launch_cols_fused_reg_m<R, RAD, 1024>(H, g, tw, twn_log2, p, s);
 }
 
 template <typename R>
@@ -827,5 +904,26 @@ cudaError_t launch_twiddles(void* tw, int twn_log2, cudaStream_t s) {
 
 
 
+
+
+// Explicit instantiations, in three groups so that each precision compiles as
+// three translation units in parallel.
+#define SFFT_INSTANTIATE_ROWS(R)                                                                   \
+    template cudaError_t launch_rows_r2c<R>(const R*, void*, long long, int, int, const void*,     \
+                                            int, cudaStream_t);                                    \
+    template cudaError_t launch_rows_c2r<R>(const void*, R*, long long, int, int, const void*,     \
+                                            int, int*, cudaStream_t);                              \
+    template cudaError_t launch_twiddles<R>(void*, int, cudaStream_t);                            \
+    template cudaError_t launch_vtable<R>(void*, const SymbolParams&, long long, cudaStream_t);
+
+#define SFFT_INSTANTIATE_COLS(R)                                                                   \
+    template cudaError_t launch_cols<R>(void*, const ColGeom&, int, const void*, int,              \
+                                        cudaStream_t);
+
+#define SFFT_INSTANTIATE_FUSED(R)                                                                  \
+    template cudaError_t launch_fused_1d<R>(R*, int, int, const void*, int, const SymbolParams&,   \
+                                            int*, cudaStream_t, const RowTables*);                 \
+    template cudaError_t launch_cols_fused<R>(void*, const ColGeom&, const void*, int,             \
+                                              const SymbolSet&, cudaStream_t);
 
 }  // namespace sfft
