@@ -37,6 +37,13 @@ template <typename R>
 cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int twn_log2,
                             const SymbolParams& p, int* status, cudaStream_t s,
                             const RowTables* rtab = nullptr);
+// 1-D axes whose packed length n = 2^(n1_log2 + n2_log2) exceeds one CTA:
+// column FFT, fused row pairs (split, multiplier, inverse split), inverse
+// column FFT, in place on `items` stacked grids.
+template <typename R>
+cudaError_t launch_fused_1d_pairs(R* grid, int n1_log2, int n2_log2, int items, const void* tw,
+                                  int twn_log2, const SymbolParams& p, int* status,
+                                  cudaStream_t s);
 template <typename R>
 cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, int nrows,
                             const void* tw, int twn_log2, cudaStream_t s);

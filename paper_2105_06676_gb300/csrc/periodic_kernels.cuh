@@ -562,6 +562,139 @@ k_cols_fused_reg(typename CxOf<R>::T* __restrict__ H, const __grid_constant__ Co
 
 
 
+// ---------------------------------------------------------------------------
+// 1-D real axes longer than one CTA holds (n = L/2 complex > 16 x threads):
+// the packed sequence z (z[m] = a[2m] + i a[2m+1]) is viewed as an n1 x n2
+// matrix, z[m1 n2 + m2]. A forward column FFT (length n1, k_cols_reg) leaves
+// column m2's k1-th output at (k1, m2); this kernel multiplies it by
+// w_n^{m2 k1}, transforms each row (length n2) and finds Z[k1 + n1 k2] at
+// (k1, k2) -- the Multi-FFT's "transposed" order, never stored transposed.
+// The real split pairs Z[k] with Z[n - k], which lies in row n1 - k1 (row 0
+// and row n1/2 pair with themselves), so each CTA takes two rows of a pair,
+// splits, multiplies by V = Lambda^T / N at the natural frequency k, undoes
+// the split, runs the inverse row transforms and the conjugate twiddle; the
+// inverse column FFT then returns a_T in natural order.
+// ---------------------------------------------------------------------------
+
+// Survivors of a 1-D row-pair thread: element r has frequency row + n1 (j + q r).
+template <typename C, typename View>
+__device__ __noinline__ void multiply_survivors_1d(View sm, int j, int q, unsigned mask,
+                                                   const SymbolParams& p, int row, int n1) {
+    using R = decltype(C{}.x);
+    while (mask) {
+        const int r = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int k[3] = {row + n1 * (j + q * r), 0, 0};
+        const double2 v = lambda_pow64(p, k);
+        const C V{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+        C& e = sm[j + q * r];
+        e = cmul(e, V);
+    }
+}
+
+template <typename R, int RAD>
+__global__ void __launch_bounds__(256)
+k_fused_1d_pairs(R* __restrict__ grid, int n1_log2, int n2_log2,
+                 const typename CxOf<R>::T* __restrict__ tw, int twn_log2,
+                 const __grid_constant__ SymbolParams p, int* status) {
+    using C = typename CxOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* small = reinterpret_cast<C*>(smraw);
+    const int n1 = 1 << n1_log2, n2 = 1 << n2_log2;
+    const int n_log2 = n1_log2 + n2_log2;
+    const long long n = 1ll << n_log2;
+    const int q = n2 >> 4;
+    const int ss = seq_stride(n2);
+    const int h = threadIdx.x / q, j = threadIdx.x - h * q;
+    const int P = blockIdx.x;
+    const bool selfp = P == 0;                       // rows 0 and n1/2 pair with themselves
+    const int row = selfp ? (h ? n1 / 2 : 0) : (h ? n1 - P : P);
+    const int prow_half = selfp ? h : 1 - h;         // half holding the partner row
+    const SeqView<C> sm{small + h * ss};
+    const SeqView<C> pm{small + prow_half * ss};
+    C* xslot = small + 2 * ss;                       // Y[n] for the inverse split
+    C* rowp = reinterpret_cast<C*>(grid) + (long long)blockIdx.y * n + (long long)row * n2;
+    const int shn = twn_log2 - n_log2;               // w_n^x = tw[x << shn]
+    const int sh2 = shn - 1;                         // W^k = exp(-2 pi i k / 2n) = tw[k << sh2]
+    const int nmask = (int)(n - 1);
+    C v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int m2 = j + q * s;
+        v[s] = cmul(rowp[m2], twiddle(tw, ((m2 * row) & nmask) << shn, -1));
+    }
+    reg_fft<-1>(v, sm, j, n2_log2, tw, twn_log2);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+    __syncthreads();
+    // partner of (row, k2): (0, (n2 - k2) mod n2) in row 0, else (n1 - row, n2 - 1 - k2)
+    auto partner = [&](int k2) { return row == 0 ? ((n2 - k2) & (n2 - 1)) : (n2 - 1 - k2); };
+    C xn{0, 0};
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k2 = j + q * r;
+        const int k = row + n1 * k2;
+        const C zk = v[r];
+        const C znk = pm[partner(k2)];
+        const C xe = cscale(cadd(zk, cconj(znk)), (R)0.5);
+        const C xo = cscale(cmul_mi(csub(zk, cconj(znk))), (R)0.5);
+        v[r] = cadd(xe, cmul(twiddle(tw, k << sh2, -1), xo));
+        if (k == 0) xn = csub(xe, xo);
+    }
+    __syncthreads();
+    // Y[k] = V[k] X[k]
+    if (p.T == 0) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], (R)p.scale);
+    } else {
+        ColSymbol<RAD> cs;
+        int kz[3] = {0, 0, 0};
+        col_symbol_init<RAD>(p, kz, cs);
+        unsigned mask = 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float2 l = col_lambda32<RAD>(p, cs, row + n1 * (j + q * r));
+            if (l.x * l.x + l.y * l.y < p.tau2) v[r] = C{(R)0, (R)0};
+            else mask |= 1u << r;
+        }
+        if (mask) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+            multiply_survivors_1d<C>(sm, j, q, mask, p, row, n1);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = mask >> r & 1 ? sm[j + q * r] : C{(R)0, (R)0};
+        }
+    }
+    if (row == 0 && j == 0) xn = multiply_single<C>(xn, p, (int)n, 0, 0);
+    __syncthreads();
+    // inverse split: Z'[k] = (Y[k] + conj Y[n-k]) + i conj(W^k) (Y[k] - conj Y[n-k])
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
+    if (row == 0 && j == 0) *xslot = xn;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k2 = j + q * r;
+        const int k = row + n1 * k2;
+        const C yk = v[r];
+        const C ynk = k == 0 ? *xslot : pm[partner(k2)];
+        const C wk = twiddle(tw, k << sh2, -1);
+        v[r] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
+    }
+    __syncthreads();
+    reg_fft<+1>(v, sm, j, n2_log2, tw, twn_log2);
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int m2 = j + q * s;
+        const C x = cmul(v[s], twiddle(tw, ((m2 * row) & nmask) << shn, +1));
+        bad |= !finite2(x);
+        rowp[m2] = x;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+
 static int threads_for(long long elems, int max_threads) {
     long long t = (elems + kEPT - 1) / kEPT;
     t = (t + 31) / 32 * 32;
@@ -781,6 +914,50 @@ cudaError_t launch_fused_1d(R* grid, int n_log2, int nrows, const void* tw, int 
     return cudaGetLastError();
 }
 
+// Large 1-D axes: forward column FFT, fused row pairs, inverse column FFT
+// (all in place on the grid viewed as n1 x n2 complex, `items` grids stacked).
+template <typename R>
+cudaError_t launch_fused_1d_pairs(R* grid, int n1_log2, int n2_log2, int items, const void* tw,
+                                  int twn_log2, const SymbolParams& p, int* status,
+                                  cudaStream_t s) {
+    using C = typename CxOf<R>::T;
+    const int n2 = 1 << n2_log2;
+    if (n1_log2 < 4 || n2_log2 < 4 || n2 / 8 > 256) return cudaErrorInvalidValue;
+    ColGeom g;
+    g.log2n = n1_log2;
+    g.S = n2;
+    g.outer = items;
+    g.os = (long long)n2 << n1_log2;
+    g.mid = 1;
+    g.ms = 0;
+    g.inner_valid = n2;
+    g.cols_log2 = 0;
+    cudaError_t err = launch_cols<R>(grid, g, -1, tw, twn_log2, s);
+    if (err != cudaSuccess) return err;
+    const size_t smem = (size_t)(2 * seq_stride(n2) + 1) * sizeof(C);
+    const dim3 blocks(1u << (n1_log2 - 1), items);
+    const int threads = n2 / 8;
+    switch (p.r) {
+#define SFFT_PAIRS(RAD)                                                                            \
+    case RAD:                                                                                      \
+        err = set_smem(k_fused_1d_pairs<R, RAD>, smem);                                           \
+        if (err != cudaSuccess) return err;                                                        \
+        k_fused_1d_pairs<R, RAD><<<blocks, threads, smem, s>>>(grid, n1_log2, n2_log2,             \
+                                                                static_cast<const C*>(tw),        \
+                                                                twn_log2, p, status);              \
+        break;
+        SFFT_PAIRS(0)
+        SFFT_PAIRS(1)
+        SFFT_PAIRS(2)
+        default:
+        SFFT_PAIRS(3)
+#undef SFFT_PAIRS
+    }
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    return launch_cols<R>(grid, g, +1, tw, twn_log2, s);
+}
+
 template <typename R>
 cudaError_t launch_rows_r2c(const R* grid, void* H, long long Mp, int n_log2, int nrows,
                             const void* tw, int twn_log2, cudaStream_t s) {
@@ -921,9 +1098,13 @@ cudaError_t launch_twiddles(void* tw, int twn_log2, cudaStream_t s) {
                                         cudaStream_t);
 
 #define SFFT_INSTANTIATE_FUSED(R)                                                                  \
+    extern template cudaError_t launch_cols<R>(void*, const ColGeom&, int, const void*, int,       \
+                                               cudaStream_t);                                      \
     template cudaError_t launch_fused_1d<R>(R*, int, int, const void*, int, const SymbolParams&,   \
                                             int*, cudaStream_t, const RowTables*);                 \
     template cudaError_t launch_cols_fused<R>(void*, const ColGeom&, const void*, int,             \
-                                              const SymbolSet&, cudaStream_t);
+                                              const SymbolSet&, cudaStream_t);                  \
+    template cudaError_t launch_fused_1d_pairs<R>(R*, int, int, int, const void*, int,             \
+                                                  const SymbolParams&, int*, cudaStream_t);
 
 }  // namespace sfft

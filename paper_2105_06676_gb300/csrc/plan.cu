@@ -80,6 +80,7 @@ int ilog2_exact(int64_t v) {
 int64_t max_axis(int ndim, int precision, int axis) {
     if (ndim < 1 || ndim > 3 || axis < 0 || axis >= ndim) return 0;
     const bool f32 = precision == STENCIL_FP32;
+    if (ndim == 1) return int64_t(1) << 24;              // longer than 2 x 16 x threads: n1 x n2 passes
     if (axis == ndim - 1) return f32 ? 32768 : 16384;   // real rows: n = L/2 complex in one CTA
     return f32 ? 16384 : 8192;                           // strided complex columns
 }
@@ -238,6 +239,15 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     cudaError_t err;
     if (d == 1) {
         // every item of a 1-D batch has the one orientation
+        if (n > 16 * (sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64)) {
+            // longer than one CTA holds: n = n1 x n2 passes; Lambda^T per element
+            if (vitems) return cudaErrorInvalidValue;
+            const int n2_log2 = std::min(11, (n_log2 + 1) / 2);   // two rows per 256-thread CTA
+            PROF_LAUNCH(PASS_FUSED_1D,
+                        launch_fused_1d_pairs<R>(S, n_log2 - n2_log2, n2_log2, items, tw, twn_log2,
+                                                 ss.p[0], status, s));
+            return cudaSuccess;
+        }
         RowTables rt;
         for (int i = 0; i < kMaxItems; ++i) rt.t[i] = ss.vtab_item[i];
         PROF_LAUNCH(PASS_FUSED_1D, launch_fused_1d<R>(S, n_log2, items, tw, twn_log2, ss.p[0],

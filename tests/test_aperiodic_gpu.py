@@ -173,3 +173,13 @@ def test_concurrent_plans_on_separate_streams():
         ref = oracle.stencil_loop(a0, w, T, "dirichlet")
         assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[prec], (a0.shape, T)
         plan.close()
+
+
+@pytest.mark.parametrize("L,precision", [(1 << 16, "fp32"), (1 << 15, "fp64"), (1 << 17, "fp32")])
+@pytest.mark.parametrize("r,T", [(1, 50), (2, 300), (3, 7)])
+def test_long_1d_dirichlet_matches_loop(L, precision, r, T):
+    # interior and strips run the n1 x n2 passes of long 1-D axes
+    w = wl.weights_random_box(1, r, 90 + T)
+    a0 = wl.grid_uniform((L,), 91 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    assert err_rel(run_gpu(a0, w, T, precision), ref, a0) <= TOL[precision]

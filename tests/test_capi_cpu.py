@@ -78,7 +78,8 @@ def _plan(lib, dims, radius, boundary=0, precision=1, weights=None):
     ((2,), 0, 0, 1, -1),                # axis shorter than 4
     ((4,), 2, 0, 1, -1),                # axis shorter than 2r+1
     ((12,), 1, 0, 1, -7),               # not a power of two
-    ((1 << 20,), 1, 0, 1, -7),          # beyond the single-CTA 1-D limit
+    ((1 << 25,), 1, 0, 1, -7),          # beyond the 1-D limit of 2^24
+    ((8, 1 << 16), 1, 0, 1, -7),        # beyond the single-CTA row limit
 ])
 def test_plan_rejects_bad_arguments(lib, dims, radius, boundary, precision, code):
     if len(dims) == 0:
@@ -118,6 +119,9 @@ def test_size_limits_and_workspace(lib):
     assert lib.stencil_max_axis(2, 1, 1) >= 8192
     assert lib.stencil_max_axis(2, 1, 0) >= 8192
     assert lib.stencil_max_axis(4, 1, 0) == 0
+    # 1-D: up to 2^24 in both precisions (n1 x n2 passes beyond one CTA)
+    assert lib.stencil_max_axis(1, 1, 0) == 1 << 24
+    assert lib.stencil_max_axis(1, 0, 0) == 1 << 24
     d = (ctypes.c_int64 * 2)(4096, 4096)
     # half spectrum 4096 x (2048 + 1 padded to 2064) complex float
     assert lib.stencil_workspace_bytes(2, d, 1, 0, 1) == 4096 * 2064 * 8

@@ -218,3 +218,55 @@ def test_profile_counts_launches():
     assert {k: v[1] for k, v in prof.items()} == {"rows_r2c": 3, "cols_fused": 3, "rows_c2r": 3}
     assert all(v[0] > 0 for v in prof.values())
     plan.close()
+
+
+# 1-D axes longer than one CTA holds (FP32 above 2^15, FP64 above 2^14): the
+# packed sequence runs as n1 x n2 passes with the spectrum in k1 + n1 k2 order.
+LONG_1D = [(1 << 15, "fp64"), (1 << 16, "fp32"), (1 << 16, "fp64"), (1 << 17, "fp32"),
+           (1 << 19, "fp32"), (1 << 20, "fp64")]
+
+
+@pytest.mark.parametrize("L,precision", LONG_1D)
+@pytest.mark.parametrize("kind,r", [("sym", 1), ("asym", 2), ("asym", 3)])
+@pytest.mark.parametrize("T", [1, 7, 100])
+def test_long_1d_matches_loop(L, precision, kind, r, T):
+    if L * T > 2e7:
+        pytest.skip("loop oracle too slow for this combination")
+    w = weights_for(1, kind, r, 40 + r + T)
+    a0 = wl.grid_uniform((L,), 11 + T)
+    ref = oracle.stencil_loop(a0, w, T, "periodic")
+    assert err_rel(run_gpu(a0, w, T, precision), ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("L,precision", [(1 << 21, "fp32"), (1 << 22, "fp64"), (1 << 24, "fp32")])
+@pytest.mark.parametrize("T", [3, 1000, 100000])
+def test_long_1d_full_size_vs_spectral_oracle(L, precision, T):
+    w = weights_for(1, "asym", 2, 77)
+    a0 = wl.grid_uniform((L,), 5)
+    ref = oracle.stencil_fft_periodic(a0, w, T)
+    assert err_rel(run_gpu(a0, w, T, precision), ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_long_1d_fourier_mode_closed_form(precision):
+    # a_0 = cos(2 pi k x / L) with symmetric weights: a_T = lambda(k)^T a_0, lambda real
+    L, T = 1 << 22, 5000
+    w = np.array([0.2, 0.6, 0.2])
+    x = np.arange(L)
+    got = []
+    for k in (1, 37, L // 2 - 3):
+        a0 = np.cos(2 * np.pi * k * x / L)
+        lam = 0.6 + 0.4 * np.cos(2 * np.pi * k / L)
+        got.append(err_rel(run_gpu(a0, w, T, precision), lam ** T * a0, a0))
+    assert max(got) <= TOL[precision]
+
+
+def test_long_1d_nyquist_and_mean():
+    # the Nyquist mode (-1)^x and the mean survive exactly as lambda(L/2)^T and 1
+    L, T = 1 << 18, 9
+    w = np.array([0.1, 0.7, 0.2])
+    x = np.arange(L)
+    a0 = 0.5 + (-1.0) ** x
+    lam_nyq = 0.7 - 0.1 - 0.2
+    ref = 0.5 + lam_nyq ** T * (-1.0) ** x
+    assert err_rel(run_gpu(a0, w, T, "fp64"), ref, a0) <= 1e-12
