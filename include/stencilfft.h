@@ -125,9 +125,29 @@ int stencil_status(stencil_plan_t plan, void* stream);
  * Base-case cutoff of RecursiveBoundary for zero-Dirichlet plans (paper
  * Fig. "stencil-fft-algorithm-1D-aperiodic", Base Case): subproblems with
  * T < cutoff are advanced by the direct loop. cutoff >= 2, or 0 for the
- * automatic choice. The result does not depend on it beyond rounding.
+ * automatic choice (a cutoff fitted to shared memory; with the AUTO schedule
+ * below, also the choice between the recursion and the direct loop). The
+ * result does not depend on it beyond rounding.
  */
 int stencil_plan_set_cutoff(stencil_plan_t plan, int64_t cutoff);
+
+/*
+ * Schedule of zero-Dirichlet plans: STENCIL_SCHEDULE_AUTO (RecursiveBoundary,
+ * paper Sec. 5, or the direct loop of Sec. 1 "Problem Specification" when a
+ * cost estimate of the boundary region says it is cheaper -- a region that
+ * covers most of the grid gains nothing from FFTs), STENCIL_SCHEDULE_RECURSIVE
+ * (always RecursiveBoundary) or STENCIL_SCHEDULE_LOOP (always the temporally
+ * blocked direct loop over the whole grid). The result does not depend on it
+ * beyond rounding. Changing it or the cutoff drops the plan's cached
+ * schedules and graphs (waits for the device). Returns STENCIL_EINVAL for a
+ * NULL plan or an unknown mode.
+ */
+enum stencil_schedule {
+    STENCIL_SCHEDULE_AUTO = 0,
+    STENCIL_SCHEDULE_RECURSIVE = 1,
+    STENCIL_SCHEDULE_LOOP = 2
+};
+int stencil_plan_set_schedule(stencil_plan_t plan, int mode);
 
 /*
  * Per-kernel timing (measurement support, not part of the paper's method).

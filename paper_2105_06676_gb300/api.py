@@ -67,6 +67,12 @@ class StencilPlan:
         _capi.check(_capi.lib().stencil_plan_set_cutoff(self._handle, int(cutoff)),
                     "stencil_plan_set_cutoff")
 
+    def set_schedule(self, mode: str) -> None:
+        """Zero-Dirichlet schedule: "auto", "recursive" or "loop" (stencil_plan_set_schedule)."""
+        code = {"auto": 0, "recursive": 1, "loop": 2}[mode]
+        _capi.check(_capi.lib().stencil_plan_set_schedule(self._handle, code),
+                    "stencil_plan_set_schedule")
+
     def run(self, grid, T: int, stream=None):
         """Advance a CUDA tensor of shape dims in place by T steps (async); returns it."""
         if not grid.is_cuda or grid.dtype != self.dtype or tuple(grid.shape) != self.dims \

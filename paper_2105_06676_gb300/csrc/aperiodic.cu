@@ -1042,8 +1042,28 @@ static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaSt
 static double fft_cell_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 8.0) * 2.0e-11; }
 static double loop_point_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 2.0) * 0.7e-12; }
 constexpr double kLaunchS = 4e-6;
+// CTAs of the base-case kernels the GPU runs at once (152 SMs, about two
+// resident tiles each): a launch with fewer tiles leaves SMs idle, so its time
+// is set by the largest tile, not by the total work.
+constexpr double kTileSlots = 304.0;
 
 static double stencil_points(const stencil_plan_s* p) { return (double)p->nweights; }
+
+// Cells (output tile plus halo) of a list of tiles, and the time-setting
+// equivalent: the total, or the largest tile times the concurrent slots.
+static double tile_cells_effective(const stencil_plan_s* p, const std::vector<BaseTile>& tiles,
+                                   int64_t halo) {
+    double total = 0.0, largest = 0.0;
+    for (const BaseTile& t : tiles) {
+        double v = 1.0;
+        for (int a = 0; a < p->ndim; ++a)
+            v *= (double)(std::min<int64_t>(t.hi[a] + halo, p->dims[a]) -
+                          std::max<int64_t>(t.lo[a] - halo, 0));
+        total += v;
+        largest = std::max(largest, v);
+    }
+    return std::max(total, largest * kTileSlots);
+}
 
 static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t T) {
     double c = 0.0;
@@ -1057,14 +1077,7 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
         if (op.kind != Op::BASE) continue;
         size_t smem = 0;
         const std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &smem);
-        double cells = 0.0;
-        for (const BaseTile& t : tiles) {
-            double v = 1.0;
-            for (int a = 0; a < p->ndim; ++a)
-                v *= (double)(std::min<int64_t>(t.hi[a] + p->radius * op.T, p->dims[a]) -
-                              std::max<int64_t>(t.lo[a] - p->radius * op.T, 0));
-            cells += v;
-        }
+        const double cells = tile_cells_effective(p, tiles, p->radius * op.T);
         c += cells * (double)op.T * stencil_points(p) * loop_point_s(p) + 2 * kLaunchS;
     }
     return c;
@@ -1085,14 +1098,7 @@ static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
         size_t smem = 0;
         const std::vector<BaseTile> tiles = make_base_tiles(p, tc, &smem, true);
         if (smem > (size_t)kSmemBudget) break;
-        double cells = 0.0;
-        for (const BaseTile& t : tiles) {
-            double v = 1.0;
-            for (int a = 0; a < p->ndim; ++a)
-                v *= (double)(std::min<int64_t>(t.hi[a] + p->radius * tc, p->dims[a]) -
-                              std::max<int64_t>(t.lo[a] - p->radius * tc, 0));
-            cells += v;
-        }
+        const double cells = tile_cells_effective(p, tiles, p->radius * tc);
         const double cost = cells * (double)T * stencil_points(p) * loop_point_s(p) +
                             (double)(T / tc + 1) * 2 * kLaunchS;
         if (best < 0 || cost < best) {
@@ -1127,13 +1133,17 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
     auto it = st->schedules.find(T);
     if (it == st->schedules.end()) {
         Schedule sc;
-        build_rb(p, sc, T, 0, auto_cutoff(p));
-        if (p->cutoff == 0) {
-            // automatic mode: the plain loop when it is the cheaper schedule (a
-            // boundary region that spans the whole grid gains nothing from FFTs)
-            Schedule loop;
-            const double c_loop = build_loop(p, loop, T);
-            if (c_loop < schedule_cost(p, sc, T)) sc = std::move(loop);
+        if (p->schedule == STENCIL_SCHEDULE_LOOP) {
+            build_loop(p, sc, T);
+        } else {
+            build_rb(p, sc, T, 0, auto_cutoff(p));
+            if (p->schedule == STENCIL_SCHEDULE_AUTO && p->cutoff == 0) {
+                // automatic mode: the plain loop when it is the cheaper schedule (a
+                // boundary region that spans the whole grid gains nothing from FFTs)
+                Schedule loop;
+                const double c_loop = build_loop(p, loop, T);
+                if (c_loop < schedule_cost(p, sc, T)) sc = std::move(loop);
+            }
         }
         assign_tables(p, sc);
         for (VTable& v : sc.tables) {
@@ -1359,6 +1369,18 @@ void aperiodic_forget_graphs(stencil_plan_s* p) {
     if (!p || !p->ap) return;
     for (auto& kv : p->ap->graphs) cudaGraphExecDestroy(kv.second);
     p->ap->graphs.clear();
+}
+
+void aperiodic_forget_schedules(stencil_plan_s* p) {
+    if (!p || !p->ap) return;
+    aperiodic_forget_graphs(p);
+    // cudaFree waits for the device, so no launch still reads these tables
+    for (auto& kv : p->ap->schedules)
+        for (auto& v : kv.second.tables) {
+            cudaFree(v.buf);
+            p->ap->bytes -= periodic_workspace_bytes(p->ndim, v.bdims, p->precision);
+        }
+    p->ap->schedules.clear();
 }
 
 size_t aperiodic_bytes(const stencil_plan_s* p) { return p && p->ap ? p->ap->bytes : 0; }

@@ -519,7 +519,15 @@ void plan_set_weights(stencil_plan_s* p, int radius, const double* w) {
 
 extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     if (!p || (cutoff != 0 && cutoff < 2)) return STENCIL_EINVAL;
+    if (p->cutoff != cutoff) aperiodic_forget_schedules(p);
     p->cutoff = cutoff;
+    return STENCIL_OK;
+}
+
+extern "C" int stencil_plan_set_schedule(stencil_plan_t p, int mode) {
+    if (!p || mode < STENCIL_SCHEDULE_AUTO || mode > STENCIL_SCHEDULE_LOOP) return STENCIL_EINVAL;
+    if (p->schedule != mode) aperiodic_forget_schedules(p);
+    p->schedule = mode;
     return STENCIL_OK;
 }
 

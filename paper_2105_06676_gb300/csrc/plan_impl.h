@@ -72,6 +72,7 @@ struct stencil_plan_s {
     // zero-Dirichlet schedule and buffers (aperiodic.cu)
     AperiodicState* ap = nullptr;
     int64_t cutoff = 0;  // 0: automatic
+    int schedule = 0;    // STENCIL_SCHEDULE_AUTO, _RECURSIVE or _LOOP
     Profiler prof;
     bool use_graphs = true;   // replay zero-Dirichlet runs as CUDA graphs
     size_t dev_bytes = 0;     // device memory this plan holds
@@ -102,5 +103,7 @@ int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
 void aperiodic_release(stencil_plan_s* p);
 // drop captured graphs (their kernel parameters hold the plan's weights)
 void aperiodic_forget_graphs(stencil_plan_s* p);
+// Drops the cached per-T schedules (and their graphs and Lambda^T tables).
+void aperiodic_forget_schedules(stencil_plan_s* p);
 // device bytes held by the zero-Dirichlet machinery of a plan
 size_t aperiodic_bytes(const stencil_plan_s* p);

@@ -183,3 +183,30 @@ def test_long_1d_dirichlet_matches_loop(L, precision, r, T):
     a0 = wl.grid_uniform((L,), 91 + T)
     ref = oracle.stencil_loop(a0, w, T, "dirichlet")
     assert err_rel(run_gpu(a0, w, T, precision), ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("dims,r,T", [((64,), 2, 45), ((64, 32), 1, 40), ((16, 16, 32), 2, 9),
+                                      ((256, 256), 1, 300)])
+def test_schedule_modes_agree_with_loop(dims, r, T):
+    # the same plan under each schedule (switching drops the cached schedule
+    # and graph of the previous mode) must match the loop oracle
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(len(dims), r, 15 + T)
+    a0 = wl.grid_uniform(dims, 16 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    plan = StencilPlan(dims, w, "dirichlet", "fp32")
+    g = torch.empty(dims, dtype=torch.float32, device="cuda")
+    for mode in ("recursive", "loop", "auto", "recursive", "loop"):
+        plan.set_schedule(mode)
+        for _ in range(2):                      # eager run, then graph replay
+            g.copy_(torch.tensor(a0, dtype=torch.float32))
+            plan.run(g, T)
+            assert plan.status() == 0
+            assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4, mode
+    plan.set_cutoff(3)                          # a new cutoff also drops the cache
+    g.copy_(torch.tensor(a0, dtype=torch.float32))
+    plan.set_schedule("recursive")
+    plan.run(g, T)
+    assert plan.status() == 0
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4
+    plan.close()
