@@ -25,6 +25,16 @@
  * Precision: STENCIL_FP64 grids are double and every step runs in FP64.
  * STENCIL_FP32 grids are float; the FFT passes run in FP32 while the symbol
  * Lambda and its T-th power are evaluated in FP64 on the GPU and rounded once.
+ * STENCIL_FP32_GEMM_* grids are float and run as STENCIL_FP32, except that
+ * every 16-point DFT of the transforms along the strided axes (all axes but
+ * the last) is a GEMM on the tensor cores (tcgen05, FP32 accumulation) with
+ * bf16 or fp16 operands, or with bf16 hi + lo split operands (three products).
+ * The single-term variants carry the operand rounding (about 2^-9 for bf16,
+ * 2^-12 for fp16 per stage) into the result and are not expected to meet the
+ * FP32 path's accuracy; the split variant is. GEMM plans are periodic, d = 2
+ * or 3, with every strided axis between 256 and 4096 (else
+ * STENCIL_EUNSUPPORTED); an abandoned tensor-core wait makes stencil_status
+ * return STENCIL_ETIMEOUT.
  *
  * Supported sizes: every l_k a power of two with l_k >= 2r + 1 and l_k >= 4.
  * Limits per precision are reported by stencil_max_axis().
@@ -52,7 +62,13 @@ extern "C" {
 typedef struct stencil_plan_s* stencil_plan_t;
 
 enum stencil_boundary { STENCIL_PERIODIC = 0, STENCIL_ZERO_DIRICHLET = 1 };
-enum stencil_precision { STENCIL_FP64 = 0, STENCIL_FP32 = 1 };
+enum stencil_precision {
+    STENCIL_FP64 = 0,
+    STENCIL_FP32 = 1,
+    STENCIL_FP32_GEMM_BF16 = 2,    /* FP32 grid; strided-axis radix-16 DFTs as bf16 GEMMs */
+    STENCIL_FP32_GEMM_FP16 = 3,    /* the same with fp16 operands */
+    STENCIL_FP32_GEMM_BF16X3 = 4   /* bf16 hi + lo split operands, three products */
+};
 
 enum stencil_status_code {
     STENCIL_OK = 0,
@@ -73,7 +89,7 @@ enum stencil_status_code {
  *   radius    r >= 0 (paper's sigma for box stencils).
  *   weights   host array of (2r+1)^ndim doubles (copied).
  *   boundary  STENCIL_PERIODIC or STENCIL_ZERO_DIRICHLET.
- *   precision STENCIL_FP64 or STENCIL_FP32.
+ *   precision STENCIL_FP64, STENCIL_FP32 or STENCIL_FP32_GEMM_*.
  * Allocates the FFT workspace and the twiddle and symbol tables on the
  * current CUDA device and builds them there (twiddles by FP64 sincospi,
  * paper Sec. 4 "Step 1").

@@ -15,6 +15,9 @@ STENCIL_PERIODIC = 0
 STENCIL_ZERO_DIRICHLET = 1
 STENCIL_FP64 = 0
 STENCIL_FP32 = 1
+STENCIL_FP32_GEMM_BF16 = 2
+STENCIL_FP32_GEMM_FP16 = 3
+STENCIL_FP32_GEMM_BF16X3 = 4
 
 STATUS = {
     0: "STENCIL_OK", -1: "STENCIL_EINVAL", -2: "STENCIL_ENOMEM", -3: "STENCIL_ECUDA",

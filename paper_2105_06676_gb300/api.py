@@ -14,7 +14,11 @@ from . import _capi
 
 _BOUNDARY = {"periodic": _capi.STENCIL_PERIODIC, "dirichlet": _capi.STENCIL_ZERO_DIRICHLET,
              "zero_dirichlet": _capi.STENCIL_ZERO_DIRICHLET}
-_PRECISION = {"fp64": _capi.STENCIL_FP64, "fp32": _capi.STENCIL_FP32}
+_PRECISION = {"fp64": _capi.STENCIL_FP64, "fp32": _capi.STENCIL_FP32,
+              # FP32 grids with the strided-axis radix-16 DFTs on the tensor cores
+              "fp32_gemm_bf16": _capi.STENCIL_FP32_GEMM_BF16,
+              "fp32_gemm_fp16": _capi.STENCIL_FP32_GEMM_FP16,
+              "fp32_gemm_bf16x3": _capi.STENCIL_FP32_GEMM_BF16X3}
 
 
 def _stream_ptr(stream):
@@ -57,7 +61,7 @@ class StencilPlan:
     @property
     def dtype(self):
         import torch
-        return torch.float32 if self.precision == "fp32" else torch.float64
+        return torch.float64 if self.precision == "fp64" else torch.float32
 
     @property
     def handle(self):

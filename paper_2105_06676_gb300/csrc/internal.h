@@ -64,6 +64,15 @@ cudaError_t launch_axis_table(double2* E64, float2* E32, int len, cudaStream_t s
 cudaError_t launch_symbol_table(double2* out, const SymbolParams& p, int nlast_half,
                                 long long total, cudaStream_t s);
 
+// Strided-axis transforms with the radix-16 DFTs on the tensor cores (FP32
+// data; mode kGemmBF16 / kGemmFP16 / kGemmBF16x3; 2^8 <= n <= 2^12). Device
+// waits that give up set bit 4 of *status.
+bool gemm_axis_ok(int log2n);
+cudaError_t launch_cols_gemm(void* H, const ColGeom& g, int dir, const void* tw, int twn_log2,
+                             int mode, int* status, cudaStream_t s);
+cudaError_t launch_cols_fused_gemm(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                                   const SymbolSet& p, int mode, int* status, cudaStream_t s);
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);
 

@@ -1,0 +1,245 @@
+// FP32 column passes with the radix-16 butterflies on the tensor cores
+// (dft_gemm.cuh): the precision variants STENCIL_FP32_GEMM_BF16 / _FP16 /
+// _BF16X3 of the Multi-FFT's strided-axis transforms (paper Sec. 4). Same
+// Stockham order, twiddles, exchanges and fused multiplier as the CUDA-core
+// column kernels; only the 16-point DFT of each stage is a GEMM.
+//
+// One CTA = 256 threads = 256 butterflies = 4096 / n interleaved columns of a
+// transform of length n (256 <= n <= 4096).
+#include <cuda_runtime.h>
+
+#include "dft_gemm.cuh"
+#include "fft_reg.cuh"
+#include "internal.h"
+#include "symbol.cuh"
+
+namespace sfft {
+
+// Transform of the thread's sequence with the GEMM butterflies (cf. reg_fft).
+template <int DIR, int MODE>
+__device__ __forceinline__ void gemm_fft(float2* v, const ColView<float2>& sm, int j, int log2n,
+                                         const float2* __restrict__ tw, int twn_log2,
+                                         DftGemm<MODE>& gm) {
+    const int n = 1 << log2n;
+    const int q = n >> 4;
+    const int r0log = (log2n & 3) ? (log2n & 3) : 4;
+    const int R0 = 1 << r0log;
+    switch (r0log) {
+        case 1: reg_first_stage<2, DIR>(v); break;
+        case 2: reg_first_stage<4, DIR>(v); break;
+        case 3: reg_first_stage<8, DIR>(v); break;
+        default: gm.template dft16<DIR>(v); break;
+    }
+    int Ns = R0;
+    bool prev_first = true;
+    while (Ns < n) {
+        if (prev_first) {
+            const int G = 16 >> r0log;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int t = i >> r0log;
+                const int r = i & (R0 - 1);
+                if (t < G) sm[(j + q * t) * R0 + r] = v[i];
+            }
+        } else {
+            const int pN = Ns >> 4;
+            const int k = j & (pN - 1);
+            const int d0 = (j - k) * 16 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) sm[d0 + pN * r] = v[r];
+        }
+        prev_first = false;
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s] = sm[j + q * s];
+        __syncthreads();
+        const int k = j & (Ns - 1);
+        const int ns_log2 = __ffs(Ns) - 1;
+        reg_twiddle<DIR>(v, k, twn_log2 - ns_log2 - 4, tw);
+        gm.template dft16<DIR>(v);
+        Ns <<= 4;
+    }
+}
+
+// Shared memory of the GEMM column kernels: the exchange buffer, then (128-byte
+// aligned) the GEMM operands and mbarrier, then the tensor-memory slot.
+template <int MODE>
+static size_t gemm_smem_bytes(int log2n) {
+    const int n = 1 << log2n;
+    const size_t ex = ((size_t)colview_elems(n, 4096 / n) * sizeof(float2) + 127) / 128 * 128;
+    return ex + DftGemm<MODE>::smem_bytes() + 16;
+}
+
+template <int MODE>
+struct GemmCarve {
+    float2* ex;
+    unsigned char* g;
+    uint32_t* slot;
+    __device__ GemmCarve(unsigned char* raw, int log2n) {
+        const int n = 1 << log2n;
+        const size_t exb =
+            ((size_t)colview_elems(n, 4096 / n) * sizeof(float2) + 127) / 128 * 128;
+        ex = reinterpret_cast<float2*>(raw);
+        g = raw + exb;
+        slot = reinterpret_cast<uint32_t*>(g + DftGemm<MODE>::smem_bytes());
+    }
+};
+
+template <int DIR, int MODE>
+__global__ void __launch_bounds__(kGemmRows)
+k_cols_gemm(float2* __restrict__ H, const __grid_constant__ ColGeom g,
+            const float2* __restrict__ tw, int twn_log2, int* status) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    GemmCarve<MODE> cv(smraw, g.log2n);
+    DftGemm<MODE> gm;
+    gm.init(cv.g, cv.slot, status);
+    const int n = 1 << g.log2n, q = n >> 4;
+    const int cl = 12 - g.log2n;
+    const int c = threadIdx.x & ((1 << cl) - 1), j = threadIdx.x >> cl;
+    const int i0 = blockIdx.x << cl;
+    const bool live = i0 + c < g.inner_valid;
+    const ColView<float2> sm{cv.ex, c, cl};
+    float2* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : float2{0, 0};
+    gemm_fft<DIR, MODE>(v, sm, j, g.log2n, tw, twn_log2, gm);
+    if (live) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
+    }
+    gm.finish();
+}
+
+template <int RAD, int MODE>
+__global__ void __launch_bounds__(kGemmRows)
+k_cols_fused_gemm(float2* __restrict__ H, const __grid_constant__ ColGeom g,
+                  const float2* __restrict__ tw, int twn_log2,
+                  const __grid_constant__ SymbolSet ps, int* status) {
+    const SymbolParams& p = ps.p[ps.orient[blockIdx.z]];
+    extern __shared__ __align__(128) unsigned char smraw[];
+    GemmCarve<MODE> cv(smraw, g.log2n);
+    DftGemm<MODE> gm;
+    gm.init(cv.g, cv.slot, status);
+    const int n = 1 << g.log2n, q = n >> 4;
+    const int cl = 12 - g.log2n;
+    const int c = threadIdx.x & ((1 << cl) - 1), j = threadIdx.x >> cl;
+    const int i0 = blockIdx.x << cl;
+    const bool live = i0 + c < g.inner_valid;
+    const ColView<float2> sm{cv.ex, c, cl};
+    float2* base = H + (long long)blockIdx.z * g.os + (long long)blockIdx.y * g.ms + i0 + c;
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? base[(long long)(j + q * s) * g.S] : float2{0, 0};
+    gemm_fft<-1, MODE>(v, sm, j, g.log2n, tw, twn_log2, gm);
+    int k[3];
+    if (p.ndim == 2) {
+        k[1] = i0 + c;
+        k[2] = 0;
+    } else {
+        k[1] = blockIdx.y;
+        k[2] = i0 + c;
+    }
+    const float2* vt = static_cast<const float2*>(
+        ps.vtab_item[blockIdx.z] ? ps.vtab_item[blockIdx.z] : ps.vtab[ps.orient[blockIdx.z]]);
+    if (vt) {
+        const float2* vbase = vt + (long long)blockIdx.y * g.ms + i0 + c;
+        if (live) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[r] = cmul(v[r], __ldg(vbase + (long long)(j + q * r) * g.S));
+        }
+    } else {
+        ColSymbol<RAD> cs;
+        col_symbol_init<RAD>(p, k, cs);
+        apply_multiplier<RAD>(v, sm, j, q, p, cs, k[1], k[2]);
+    }
+    __syncthreads();
+    gemm_fft<+1, MODE>(v, sm, j, g.log2n, tw, twn_log2, gm);
+    if (live) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) base[(long long)(j + q * r) * g.S] = v[r];
+    }
+    gm.finish();
+}
+
+template <typename K>
+static cudaError_t gemm_smem_optin(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return smem_optin(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+bool gemm_axis_ok(int log2n) { return log2n >= 8 && log2n <= 12; }
+
+template <int MODE>
+static cudaError_t launch_cols_gemm_m(void* H, ColGeom g, int dir, const void* tw, int twn_log2,
+                                      int* status, cudaStream_t s) {
+    const int cl = 12 - g.log2n;
+    g.cols_log2 = cl;
+    const size_t smem = gemm_smem_bytes<MODE>(g.log2n);
+    const dim3 grid((g.inner_valid + (1 << cl) - 1) >> cl, g.mid, g.outer);
+    cudaError_t err;
+    if (dir < 0) {
+        err = gemm_smem_optin(k_cols_gemm<-1, MODE>, smem);
+        if (err != cudaSuccess) return err;
+        k_cols_gemm<-1, MODE><<<grid, kGemmRows, smem, s>>>(static_cast<float2*>(H), g,
+                                                             static_cast<const float2*>(tw),
+                                                             twn_log2, status);
+    } else {
+        err = gemm_smem_optin(k_cols_gemm<+1, MODE>, smem);
+        if (err != cudaSuccess) return err;
+        k_cols_gemm<+1, MODE><<<grid, kGemmRows, smem, s>>>(static_cast<float2*>(H), g,
+                                                             static_cast<const float2*>(tw),
+                                                             twn_log2, status);
+    }
+    return cudaGetLastError();
+}
+
+template <int RAD, int MODE>
+static cudaError_t launch_cols_fused_gemm_m(void* H, ColGeom g, const void* tw, int twn_log2,
+                                            const SymbolSet& p, int* status, cudaStream_t s) {
+    const int cl = 12 - g.log2n;
+    g.cols_log2 = cl;
+    const size_t smem = gemm_smem_bytes<MODE>(g.log2n);
+    const dim3 grid((g.inner_valid + (1 << cl) - 1) >> cl, g.mid, g.outer);
+    cudaError_t err = gemm_smem_optin(k_cols_fused_gemm<RAD, MODE>, smem);
+    if (err != cudaSuccess) return err;
+    k_cols_fused_gemm<RAD, MODE><<<grid, kGemmRows, smem, s>>>(
+        static_cast<float2*>(H), g, static_cast<const float2*>(tw), twn_log2, p, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_gemm(void* H, const ColGeom& g, int dir, const void* tw, int twn_log2,
+                             int mode, int* status, cudaStream_t s) {
+    if (!gemm_axis_ok(g.log2n)) return cudaErrorInvalidValue;
+    switch (mode) {
+        case kGemmBF16: return launch_cols_gemm_m<kGemmBF16>(H, g, dir, tw, twn_log2, status, s);
+        case kGemmFP16: return launch_cols_gemm_m<kGemmFP16>(H, g, dir, tw, twn_log2, status, s);
+        case kGemmBF16x3: return launch_cols_gemm_m<kGemmBF16x3>(H, g, dir, tw, twn_log2, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MODE>
+static cudaError_t fused_gemm_r(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                                const SymbolSet& p, int* status, cudaStream_t s) {
+    switch (p.p[0].r) {
+        case 0: return launch_cols_fused_gemm_m<0, MODE>(H, g, tw, twn_log2, p, status, s);
+        case 1: return launch_cols_fused_gemm_m<1, MODE>(H, g, tw, twn_log2, p, status, s);
+        case 2: return launch_cols_fused_gemm_m<2, MODE>(H, g, tw, twn_log2, p, status, s);
+        default: return launch_cols_fused_gemm_m<3, MODE>(H, g, tw, twn_log2, p, status, s);
+    }
+}
+
+cudaError_t launch_cols_fused_gemm(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                                   const SymbolSet& p, int mode, int* status, cudaStream_t s) {
+    if (!gemm_axis_ok(g.log2n)) return cudaErrorInvalidValue;
+    switch (mode) {
+        case kGemmBF16: return fused_gemm_r<kGemmBF16>(H, g, tw, twn_log2, p, status, s);
+        case kGemmFP16: return fused_gemm_r<kGemmFP16>(H, g, tw, twn_log2, p, status, s);
+        case kGemmBF16x3: return fused_gemm_r<kGemmBF16x3>(H, g, tw, twn_log2, p, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sfft

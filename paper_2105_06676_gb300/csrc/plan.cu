@@ -267,7 +267,11 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         g.ms = 0;
         g.inner_valid = n + 1;
         g.cols_log2 = cols_log2_for(g.log2n, celem, maxt);
-        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, ss, s));
+        if (sizeof(R) == 4 && p->gemm >= 0)
+            PROF_LAUNCH(PASS_COLS_FUSED,
+                        launch_cols_fused_gemm(H, g, tw, twn_log2, ss, p->gemm, status, s));
+        else
+            PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, ss, s));
     } else {
         ColGeom g1;
         g1.log2n = ilog2_exact(len[1]);
@@ -278,7 +282,12 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         g1.ms = 0;
         g1.inner_valid = n + 1;
         g1.cols_log2 = cols_log2_for(g1.log2n, celem, maxt);
-        PROF_LAUNCH(PASS_COLS_FWD, launch_cols<R>(H, g1, -1, tw, twn_log2, s));
+        const bool gemm = sizeof(R) == 4 && p->gemm >= 0;
+        if (gemm)
+            PROF_LAUNCH(PASS_COLS_FWD,
+                        launch_cols_gemm(H, g1, -1, tw, twn_log2, p->gemm, status, s));
+        else
+            PROF_LAUNCH(PASS_COLS_FWD, launch_cols<R>(H, g1, -1, tw, twn_log2, s));
         ColGeom g0;
         g0.log2n = ilog2_exact(len[0]);
         g0.S = len[1] * Mp;
@@ -288,8 +297,15 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         g0.ms = Mp;
         g0.inner_valid = n + 1;
         g0.cols_log2 = cols_log2_for(g0.log2n, celem, maxt);
-        PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, ss, s));
-        PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
+        if (gemm) {
+            PROF_LAUNCH(PASS_COLS_FUSED,
+                        launch_cols_fused_gemm(H, g0, tw, twn_log2, ss, p->gemm, status, s));
+            PROF_LAUNCH(PASS_COLS_INV,
+                        launch_cols_gemm(H, g1, +1, tw, twn_log2, p->gemm, status, s));
+        } else {
+            PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, ss, s));
+            PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
+        }
     }
     PROF_LAUNCH(PASS_ROWS_C2R,
                 launch_rows_c2r<R>(H, S, Mp, n_log2, (int)rows, tw, twn_log2, status, s));
@@ -355,19 +371,35 @@ const char* stencil_strerror(int code) {
     }
 }
 
+static bool is_gemm(int precision) {
+    return precision >= STENCIL_FP32_GEMM_BF16 && precision <= STENCIL_FP32_GEMM_BF16X3;
+}
+// Arithmetic of the grid and of the CUDA-core passes.
+static int base_precision(int precision) { return is_gemm(precision) ? STENCIL_FP32 : precision; }
+
 int64_t stencil_max_axis(int ndim, int precision, int axis) {
-    if (precision != STENCIL_FP32 && precision != STENCIL_FP64) return 0;
-    return max_axis(ndim, precision, axis);
+    if (precision < STENCIL_FP64 || precision > STENCIL_FP32_GEMM_BF16X3) return 0;
+    if (is_gemm(precision)) {
+        if (ndim < 2 || ndim > 3 || axis < 0 || axis >= ndim) return 0;
+        if (axis < ndim - 1) return 4096;
+    }
+    return max_axis(ndim, base_precision(precision), axis);
 }
 
 static int validate(int ndim, const int64_t* dims, int radius, int boundary, int precision) {
     if (ndim < 1 || ndim > 3 || !dims || radius < 0 || radius > kMaxRadius) return STENCIL_EINVAL;
     if (boundary != STENCIL_PERIODIC && boundary != STENCIL_ZERO_DIRICHLET) return STENCIL_EINVAL;
-    if (precision != STENCIL_FP32 && precision != STENCIL_FP64) return STENCIL_EINVAL;
+    if (precision < STENCIL_FP64 || precision > STENCIL_FP32_GEMM_BF16X3) return STENCIL_EINVAL;
     for (int a = 0; a < ndim; ++a) {
         if (dims[a] < 2 * radius + 1 || dims[a] < 4) return STENCIL_EINVAL;
         if (ilog2_exact(dims[a]) < 0) return STENCIL_EUNSUPPORTED;
-        if (dims[a] > max_axis(ndim, precision, a)) return STENCIL_EUNSUPPORTED;
+        if (dims[a] > max_axis(ndim, base_precision(precision), a)) return STENCIL_EUNSUPPORTED;
+    }
+    if (is_gemm(precision)) {
+        // tensor-core DFTs: periodic, strided axes of 256..4096
+        if (boundary != STENCIL_PERIODIC || ndim < 2) return STENCIL_EUNSUPPORTED;
+        for (int a = 0; a < ndim - 1; ++a)
+            if (!gemm_axis_ok(ilog2_exact(dims[a]))) return STENCIL_EUNSUPPORTED;
     }
     return STENCIL_OK;
 }
@@ -375,7 +407,7 @@ static int validate(int ndim, const int64_t* dims, int radius, int boundary, int
 size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int boundary,
                                int precision) {
     if (validate(ndim, dims, radius, boundary, precision) != STENCIL_OK) return 0;
-    return periodic_workspace_bytes(ndim, dims, precision);
+    return periodic_workspace_bytes(ndim, dims, base_precision(precision));
 }
 
 int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
@@ -386,6 +418,8 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
     if (rc != STENCIL_OK) return rc;
     stencil_plan_s* p = new (std::nothrow) stencil_plan_s();
     if (!p) return STENCIL_ENOMEM;
+    if (is_gemm(precision)) p->gemm = precision - STENCIL_FP32_GEMM_BF16;   // kGemm* order
+    precision = base_precision(precision);
     p->ndim = ndim;
     p->radius = radius;
     p->boundary = boundary;
@@ -490,7 +524,7 @@ int stencil_status(stencil_plan_t p, void* stream) {
         err = cudaMemsetAsync(p->status, 0, sizeof(int), s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return from_cuda(err);
-        return STENCIL_ENONFINITE;
+        return (flag & 4) ? STENCIL_ETIMEOUT : STENCIL_ENONFINITE;
     }
     return STENCIL_OK;
 }

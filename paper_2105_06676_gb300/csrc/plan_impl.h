@@ -73,6 +73,7 @@ struct stencil_plan_s {
     AperiodicState* ap = nullptr;
     int64_t cutoff = 0;  // 0: automatic
     int schedule = 0;    // STENCIL_SCHEDULE_AUTO, _RECURSIVE or _LOOP
+    int gemm = -1;       // tensor-core DFT operand mode (kGemm*), -1: CUDA-core FFTs
     Profiler prof;
     bool use_graphs = true;   // replay zero-Dirichlet runs as CUDA graphs
     size_t dev_bytes = 0;     // device memory this plan holds
