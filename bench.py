@@ -373,6 +373,30 @@ def main():
         plan_x.close()
         del g_x, pris_x
 
+    # ---- tensor-core DFT variants on the 3-D configuration (secondary): the
+    # strided-axis radix-16 butterflies as tcgen05 GEMMs; time per solve and the
+    # max difference from the FP32 path relative to max|a_0|
+    wk3 = wl.star3d_512("fp32")
+    pris3 = torch.tensor(wk3.grid(), dtype=torch.float32, device="cuda")
+    g3 = pris3.clone()
+    ref_plan = StencilPlan(wk3.dims, wk3.weights, "periodic", "fp32")
+    ref_plan.run(g3, wk3.T)
+    ref3 = g3.clone()
+    ref_plan.close()
+    amax = float(pris3.abs().max())
+    gemm_lines = {}
+    for prec in ("fp32_gemm_bf16x3", "fp32_gemm_fp16", "fp32_gemm_bf16"):
+        plan_g = StencilPlan(wk3.dims, wk3.weights, "periodic", prec)
+        times_g = time_solve(plan_g, g3, pris3, flush, max(3, args.steps // 4), 3, wk3.T)
+        assert plan_g.status() == 0
+        ms_g = sorted(times_g)[len(times_g) // 2]
+        diff = float((g3 - ref3).abs().max()) / amax
+        gemm_lines[prec] = {"ms_per_step": ms_g,
+                            "value": world * wk3.n_cells * wk3.T / (ms_g * 1e-3),
+                            "max_diff_vs_fp32_rel": diff}
+        plan_g.close()
+    del g3, pris3, ref3
+
     # ---- zero-Dirichlet path (secondary): 8192^2 9-point box, T = 4096, FP32
     dirichlet = None
     if not args.no_dirichlet:
@@ -440,6 +464,7 @@ def main():
             "dirichlet_path": dirichlet,
             "heat1d_path": extra["heat1d_4096_fp64"],
             "star3d_path": extra["star7_3d_512_fp32"],
+            "star3d_tensor_core_dft": {"workload": wk3.name, **gemm_lines},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": grid_bytes,
                     "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,

@@ -86,7 +86,7 @@ struct GemmCarve {
 };
 
 template <int DIR, int MODE>
-__global__ void __launch_bounds__(kGemmRows)
+__global__ void __launch_bounds__(kGemmRows, 2)
 k_cols_gemm(float2* __restrict__ H, const __grid_constant__ ColGeom g,
             const float2* __restrict__ tw, int twn_log2, int* status) {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -112,7 +112,7 @@ k_cols_gemm(float2* __restrict__ H, const __grid_constant__ ColGeom g,
 }
 
 template <int RAD, int MODE>
-__global__ void __launch_bounds__(kGemmRows)
+__global__ void __launch_bounds__(kGemmRows, 2)
 k_cols_fused_gemm(float2* __restrict__ H, const __grid_constant__ ColGeom g,
                   const float2* __restrict__ tw, int twn_log2,
                   const __grid_constant__ SymbolSet ps, int* status) {
