@@ -430,38 +430,68 @@ k_base_3d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
     }
 }
 
-// One step of the loop on the whole 3-D grid with zero ghosts (a single
-// launch per step; used when the boundary region is the whole grid).
+// One step of the loop on the whole 3-D grid, streamed along axis 0: a CTA
+// owns a kStepTY x kStepTX tile of (axis 1, axis 2) and a chunk of axis-0
+// planes. Each input plane (with an r-cell halo, zeros outside the grid) is
+// staged once in shared memory; every thread reads its (2r+1)^2 neighbours
+// into registers and adds them, slice by slice, into a window of 2r+1
+// accumulators for the outputs z = p - r .. p + r. The oldest one is complete
+// after plane p and is stored. Per output: (2r+1)^2 shared loads and (2r+1)^3
+// FMAs, against (2r+1)^3 global loads for a direct gather.
+constexpr int kStepTX = 32, kStepTY = 8;
+
 template <typename R, int RAD>
-__global__ void __launch_bounds__(256)
-k_step_3d(const R* __restrict__ A, R* __restrict__ B, const __grid_constant__ BaseParams p) {
+__global__ void __launch_bounds__(kStepTX * kStepTY)
+k_step_3d_stream(const R* __restrict__ A, R* __restrict__ B, const __grid_constant__ BaseParams p,
+                 int zchunk) {
     constexpr int W = 2 * RAD + 1;
+    constexpr int PX = kStepTX + 2 * RAD, PY = kStepTY + 2 * RAD;
+    __shared__ R plane[PY][PX];
     const int L0 = p.gdims[0], L1 = p.gdims[1], L2 = p.gdims[2];
-    const long long n = (long long)L0 * L1 * L2;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(e % L2);
-        const long long zy = e / L2;
-        const int y = (int)(zy % L1), z = (int)(zy / L1);
-        R acc = 0;
+    const int tx = threadIdx.x % kStepTX, ty = threadIdx.x / kStepTX;
+    const int x0 = blockIdx.x * kStepTX, y0 = blockIdx.y * kStepTY;
+    const int z0 = blockIdx.z * zchunk, z1 = min(L0, z0 + zchunk);
+    const int x = x0 + tx, y = y0 + ty;
+    R acc[W];
 #pragma unroll
-        for (int m0 = 0; m0 < W; ++m0) {
-            const int zz = z + m0 - RAD;
-            if (zz < 0 || zz >= L0) continue;
-#pragma unroll
-            for (int m1 = 0; m1 < W; ++m1) {
-                const int yy = y + m1 - RAD;
-                if (yy < 0 || yy >= L1) continue;
-                const R* row = A + ((long long)zz * L1 + yy) * L2;
-#pragma unroll
-                for (int m2 = 0; m2 < W; ++m2) {
-                    const int xx = x + m2 - RAD;
-                    if (xx >= 0 && xx < L2)
-                        acc += base_weight<R>(p, (m0 * W + m1) * W + m2) * __ldg(row + xx);
-                }
+    for (int i = 0; i < W; ++i) acc[i] = 0;
+    for (int pz = z0 - RAD; pz < z1 + RAD; ++pz) {
+        const bool in = pz >= 0 && pz < L0;
+        if (in) {
+            const R* src = A + (long long)pz * L1 * L2;
+            for (int e = threadIdx.x; e < PX * PY; e += kStepTX * kStepTY) {
+                const int py = e / PX, px = e - py * PX;
+                const int gy = y0 + py - RAD, gx = x0 + px - RAD;
+                plane[py][px] = (gy >= 0 && gy < L1 && gx >= 0 && gx < L2)
+                                    ? __ldg(src + (long long)gy * L2 + gx) : R(0);
             }
         }
-        B[e] = acc;
+        __syncthreads();
+        if (in) {
+            R nb[W][W];
+#pragma unroll
+            for (int m1 = 0; m1 < W; ++m1)
+#pragma unroll
+                for (int m2 = 0; m2 < W; ++m2) nb[m1][m2] = plane[ty + m1][tx + m2];
+            // acc[i] is output z = pz - RAD + i, which takes this plane with m0 = RAD - i
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                R s = 0;
+#pragma unroll
+                for (int m1 = 0; m1 < W; ++m1)
+#pragma unroll
+                    for (int m2 = 0; m2 < W; ++m2)
+                        s += base_weight<R>(p, ((W - 1 - i) * W + m1) * W + m2) * nb[m1][m2];
+                acc[i] += s;
+            }
+        }
+        __syncthreads();
+        const int zo = pz - RAD;
+        if (zo >= z0 && zo < z1 && y < L1 && x < L2)
+            B[((long long)zo * L1 + y) * L2 + x] = acc[0];
+#pragma unroll
+        for (int i = 0; i + 1 < W; ++i) acc[i] = acc[i + 1];
+        acc[W - 1] = 0;
     }
 }
 
@@ -883,9 +913,12 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
         // chunk sizes: normal axis up to 64, other axes as large as the budget allows
         int cs[3];
         for (int b = 0; b < 3; ++b) cs[b] = b < d ? std::min(r.hi[b] - r.lo[b], b == r.normal ? 64 : 1024) : 1;
+        // staged cells of a tile: output, T_b-step halo (clipped to the grid) and
+        // the kernel's zero ring of width r on each side
         auto vol = [&](void) {
             size_t v = 1;
-            for (int b = 0; b < d; ++b) v *= (size_t)std::min(cs[b] + 2 * h, (int)p->dims[b]);
+            for (int b = 0; b < d; ++b)
+                v *= (size_t)(std::min(cs[b] + 2 * h, (int)p->dims[b]) + 2 * p->radius);
             return v;
         };
         while (vol() > budget) {
@@ -1012,17 +1045,26 @@ static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaSt
         bp.w[i] = p->weights[i];
         bp.wf[i] = (float)p->weights[i];
     }
-    const int blocks = grid_blocks(p->n_cells);
+    // tiles of (axis 1, axis 2); axis 0 cut into chunks until about four CTAs
+    // per SM are in flight, each chunk at least 2r + 2 planes deep
+    const int L0 = (int)p->dims[0];
+    const dim3 tiles((unsigned)((p->dims[2] + kStepTX - 1) / kStepTX),
+                     (unsigned)((p->dims[1] + kStepTY - 1) / kStepTY), 1);
+    const int want = std::max(1, (int)(608 / (tiles.x * tiles.y)));
+    int zchunk = std::max<int>((L0 + want - 1) / want, 2 * p->radius + 2);
+    zchunk = std::min(zchunk, L0);
+    const dim3 grid3(tiles.x, tiles.y, (unsigned)((L0 + zchunk - 1) / zchunk));
     cudaError_t err = cudaSuccess;
     R* a = X;
     R* b = Y;
     p->prof.begin(PASS_BASE_LOOP, s);
     for (int64_t t = 0; t < T && err == cudaSuccess; ++t) {
+        constexpr int TH = kStepTX * kStepTY;
         switch (p->radius) {
-            case 1: k_step_3d<R, 1><<<blocks, 256, 0, s>>>(a, b, bp); break;
-            case 2: k_step_3d<R, 2><<<blocks, 256, 0, s>>>(a, b, bp); break;
-            case 3: k_step_3d<R, 3><<<blocks, 256, 0, s>>>(a, b, bp); break;
-            default: k_step_3d<R, 0><<<blocks, 256, 0, s>>>(a, b, bp); break;
+            case 1: k_step_3d_stream<R, 1><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
+            case 2: k_step_3d_stream<R, 2><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
+            case 3: k_step_3d_stream<R, 3><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
+            default: k_step_3d_stream<R, 0><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
         }
         err = cudaGetLastError();
         R* tmp = a;
@@ -1088,9 +1130,13 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
 static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
     sc.loop = true;
     if (p->ndim == 3) {
+        // axis-0 streamed steps: FMA-bound at about 8e12 (FP32) / 3.6e11 (FP64)
+        // point updates per second on large grids, about 8 us per step on small
+        // ones (GB300 measurements)
         sc.ops.push_back(Op{Op::STEP, -1, T});
-        return (double)p->n_cells * (double)T * stencil_points(p) * loop_point_s(p) * 3.0 +
-               (double)T * kLaunchS;
+        const double per_pt = p->precision == STENCIL_FP32 ? 1.3e-13 : 2.8e-12;
+        const double step = std::max(8e-6, (double)p->n_cells * stencil_points(p) * per_pt);
+        return (double)T * (step + 2e-6);
     }
     double best = -1.0;
     int64_t best_tc = 1;

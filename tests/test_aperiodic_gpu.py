@@ -210,3 +210,40 @@ def test_schedule_modes_agree_with_loop(dims, r, T):
     assert plan.status() == 0
     assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dims,r,T", [((128, 8, 64), 1, 6), ((16, 64, 32), 3, 4),
+                                      ((256, 64, 64), 2, 3), ((8, 16, 256), 2, 5), ((4, 4, 4), 1, 9)])
+def test_3d_loop_schedule_matches_loop(dims, r, T, precision):
+    # the whole-grid 3-D loop (axis-0 streamed steps; chunks of axis 0 with halos)
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(3, r, 30 + T)
+    a0 = wl.grid_uniform(dims, 31 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(dims, w, "dirichlet", precision)
+    plan.set_schedule("loop")
+    plan.run(g, T)
+    assert plan.status() == 0
+    plan.close()
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims,T", [((32, 32, 32), 5), ((64, 64, 64), 3), ((32, 16, 64), 20)])
+def test_3d_radius3_recursion_matches_loop(dims, T, precision):
+    # radius-3 3-D tiles: the base case's zero ring counts against shared memory
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(3, 3, 50 + T)
+    a0 = wl.grid_uniform(dims, 51 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(dims, w, "dirichlet", precision)
+    plan.set_schedule("recursive")
+    plan.run(g, T)
+    assert plan.status() == 0
+    plan.close()
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
