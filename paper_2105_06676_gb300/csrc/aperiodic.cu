@@ -430,26 +430,65 @@ k_base_3d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
     }
 }
 
+// One step of the loop on the whole 3-D grid with zero ghosts, one output per
+// thread gathered directly (used for FP64, where the double-precision FMA
+// rate, not the loads, sets the time and a streamed chunk's recomputed halo
+// planes would cost FMAs).
+template <typename R, int RAD>
+__global__ void __launch_bounds__(256)
+k_step_3d(const R* __restrict__ A, R* __restrict__ B, const __grid_constant__ BaseParams p) {
+    constexpr int W = 2 * RAD + 1;
+    const int L0 = p.gdims[0], L1 = p.gdims[1], L2 = p.gdims[2];
+    const long long n = (long long)L0 * L1 * L2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e % L2);
+        const long long zy = e / L2;
+        const int y = (int)(zy % L1), z = (int)(zy / L1);
+        R acc = 0;
+#pragma unroll
+        for (int m0 = 0; m0 < W; ++m0) {
+            const int zz = z + m0 - RAD;
+            if (zz < 0 || zz >= L0) continue;
+#pragma unroll
+            for (int m1 = 0; m1 < W; ++m1) {
+                const int yy = y + m1 - RAD;
+                if (yy < 0 || yy >= L1) continue;
+                const R* row = A + ((long long)zz * L1 + yy) * L2;
+#pragma unroll
+                for (int m2 = 0; m2 < W; ++m2) {
+                    const int xx = x + m2 - RAD;
+                    if (xx >= 0 && xx < L2)
+                        acc += base_weight<R>(p, (m0 * W + m1) * W + m2) * __ldg(row + xx);
+                }
+            }
+        }
+        B[e] = acc;
+    }
+}
+
 // One step of the loop on the whole 3-D grid, streamed along axis 0: a CTA
-// owns a kStepTY x kStepTX tile of (axis 1, axis 2) and a chunk of axis-0
+// owns a TY x TX tile of (axis 1, axis 2), TX x TY = 256 with TX matched to
+// the grid's contiguous axis, and a chunk of axis-0
 // planes. Each input plane (with an r-cell halo, zeros outside the grid) is
 // staged once in shared memory; every thread reads its (2r+1)^2 neighbours
 // into registers and adds them, slice by slice, into a window of 2r+1
 // accumulators for the outputs z = p - r .. p + r. The oldest one is complete
 // after plane p and is stored. Per output: (2r+1)^2 shared loads and (2r+1)^3
 // FMAs, against (2r+1)^3 global loads for a direct gather.
-constexpr int kStepTX = 32, kStepTY = 8;
+constexpr int kStepThreads = 256;
 
-template <typename R, int RAD>
-__global__ void __launch_bounds__(kStepTX * kStepTY)
+template <typename R, int RAD, int TX>
+__global__ void __launch_bounds__(kStepThreads)
 k_step_3d_stream(const R* __restrict__ A, R* __restrict__ B, const __grid_constant__ BaseParams p,
                  int zchunk) {
     constexpr int W = 2 * RAD + 1;
-    constexpr int PX = kStepTX + 2 * RAD, PY = kStepTY + 2 * RAD;
+    constexpr int TY = kStepThreads / TX;
+    constexpr int PX = TX + 2 * RAD, PY = TY + 2 * RAD;
     __shared__ R plane[PY][PX];
     const int L0 = p.gdims[0], L1 = p.gdims[1], L2 = p.gdims[2];
-    const int tx = threadIdx.x % kStepTX, ty = threadIdx.x / kStepTX;
-    const int x0 = blockIdx.x * kStepTX, y0 = blockIdx.y * kStepTY;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zchunk, z1 = min(L0, z0 + zchunk);
     const int x = x0 + tx, y = y0 + ty;
     R acc[W];
@@ -459,7 +498,7 @@ k_step_3d_stream(const R* __restrict__ A, R* __restrict__ B, const __grid_consta
         const bool in = pz >= 0 && pz < L0;
         if (in) {
             const R* src = A + (long long)pz * L1 * L2;
-            for (int e = threadIdx.x; e < PX * PY; e += kStepTX * kStepTY) {
+            for (int e = threadIdx.x; e < PX * PY; e += kStepThreads) {
                 const int py = e / PX, px = e - py * PX;
                 const int gy = y0 + py - RAD, gx = x0 + px - RAD;
                 plane[py][px] = (gy >= 0 && gy < L1 && gx >= 0 && gx < L2)
@@ -1045,11 +1084,13 @@ static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaSt
         bp.w[i] = p->weights[i];
         bp.wf[i] = (float)p->weights[i];
     }
-    // tiles of (axis 1, axis 2); axis 0 cut into chunks until about four CTAs
-    // per SM are in flight, each chunk at least 2r + 2 planes deep
+    const int blocks = grid_blocks(p->n_cells);
+    // FP32: tiles of (axis 1, axis 2); axis 0 cut into chunks until about four
+    // CTAs per SM are in flight, each chunk at least 2r + 2 planes deep
     const int L0 = (int)p->dims[0];
-    const dim3 tiles((unsigned)((p->dims[2] + kStepTX - 1) / kStepTX),
-                     (unsigned)((p->dims[1] + kStepTY - 1) / kStepTY), 1);
+    const int TX = p->dims[2] >= 32 ? 32 : p->dims[2] >= 16 ? 16 : 8;
+    const dim3 tiles((unsigned)((p->dims[2] + TX - 1) / TX),
+                     (unsigned)((p->dims[1] + kStepThreads / TX - 1) / (kStepThreads / TX)), 1);
     const int want = std::max(1, (int)(608 / (tiles.x * tiles.y)));
     int zchunk = std::max<int>((L0 + want - 1) / want, 2 * p->radius + 2);
     zchunk = std::min(zchunk, L0);
@@ -1059,12 +1100,26 @@ static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaSt
     R* b = Y;
     p->prof.begin(PASS_BASE_LOOP, s);
     for (int64_t t = 0; t < T && err == cudaSuccess; ++t) {
-        constexpr int TH = kStepTX * kStepTY;
-        switch (p->radius) {
-            case 1: k_step_3d_stream<R, 1><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
-            case 2: k_step_3d_stream<R, 2><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
-            case 3: k_step_3d_stream<R, 3><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
-            default: k_step_3d_stream<R, 0><<<grid3, TH, 0, s>>>(a, b, bp, zchunk); break;
+        if constexpr (sizeof(R) == 8) {
+            switch (p->radius) {
+                case 1: k_step_3d<R, 1><<<blocks, 256, 0, s>>>(a, b, bp); break;
+                case 2: k_step_3d<R, 2><<<blocks, 256, 0, s>>>(a, b, bp); break;
+                case 3: k_step_3d<R, 3><<<blocks, 256, 0, s>>>(a, b, bp); break;
+                default: k_step_3d<R, 0><<<blocks, 256, 0, s>>>(a, b, bp); break;
+            }
+        } else {
+#define SFFT_STEP(RADV, TXV) \
+    k_step_3d_stream<R, RADV, TXV><<<grid3, kStepThreads, 0, s>>>(a, b, bp, zchunk)
+#define SFFT_STEP_TX(RADV)                         \
+    (TX == 32 ? SFFT_STEP(RADV, 32) : TX == 16 ? SFFT_STEP(RADV, 16) : SFFT_STEP(RADV, 8))
+            switch (p->radius) {
+                case 1: SFFT_STEP_TX(1); break;
+                case 2: SFFT_STEP_TX(2); break;
+                case 3: SFFT_STEP_TX(3); break;
+                default: SFFT_STEP_TX(0); break;
+            }
+#undef SFFT_STEP_TX
+#undef SFFT_STEP
         }
         err = cudaGetLastError();
         R* tmp = a;
@@ -1084,10 +1139,10 @@ static cudaError_t launch_steps(stencil_plan_s* p, R* X, R* Y, int64_t T, cudaSt
 static double fft_cell_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 8.0) * 2.0e-11; }
 static double loop_point_s(const stencil_plan_s* p) { return (p->precision == STENCIL_FP32 ? 1.0 : 2.0) * 0.7e-12; }
 constexpr double kLaunchS = 4e-6;
-// CTAs of the base-case kernels the GPU runs at once (152 SMs, about two
-// resident tiles each): a launch with fewer tiles leaves SMs idle, so its time
-// is set by the largest tile, not by the total work.
-constexpr double kTileSlots = 304.0;
+// Base-case tiles the GPU works on at full rate at once (one per SM of 152):
+// a launch with fewer tiles leaves SMs idle, so its time is set by the
+// largest tile, not by the total work.
+constexpr double kTileSlots = 152.0;
 
 static double stencil_points(const stencil_plan_s* p) { return (double)p->nweights; }
 
@@ -1104,7 +1159,9 @@ static double tile_cells_effective(const stencil_plan_s* p, const std::vector<Ba
         total += v;
         largest = std::max(largest, v);
     }
-    return std::max(total, largest * kTileSlots);
+    // calibrated on 3-D frames (tens of tiles); 2-D frames measured close to
+    // their total work
+    return p->ndim == 3 ? std::max(total, largest * kTileSlots) : total;
 }
 
 static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t T) {
@@ -1115,12 +1172,19 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
     for (const Step& st : sc.steps)
         for (const Batch& b : st.batches)
             c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + 6 * kLaunchS;
+    // base leaves repeat a few T_b values thousands of times: price each once
+    std::map<int64_t, double> leaf;
     for (const Op& op : sc.ops) {
         if (op.kind != Op::BASE) continue;
-        size_t smem = 0;
-        const std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &smem);
-        const double cells = tile_cells_effective(p, tiles, p->radius * op.T);
-        c += cells * (double)op.T * stencil_points(p) * loop_point_s(p) + 2 * kLaunchS;
+        auto it = leaf.find(op.T);
+        if (it == leaf.end()) {
+            size_t smem = 0;
+            const std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &smem);
+            const double cells = tile_cells_effective(p, tiles, p->radius * op.T);
+            it = leaf.emplace(op.T, cells * (double)op.T * stencil_points(p) * loop_point_s(p) +
+                                        2 * kLaunchS).first;
+        }
+        c += it->second;
     }
     return c;
 }
