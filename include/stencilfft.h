@@ -109,11 +109,15 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
 int stencil_run(stencil_plan_t plan, void* grid, int64_t T, void* stream);
 
 /*
- * End-to-end variant of stencil_run on host memory: copies host_in to a
- * plan-owned device grid, solves, copies the result to host_out and
- * synchronises the stream. host_in and host_out hold prod(dims) elements of
- * the plan's precision (pinned memory gives full copy bandwidth; they may
- * alias).
+ * End-to-end variant of stencil_run on host memory; synchronises the stream
+ * before returning. host_in and host_out hold prod(dims) elements of the
+ * plan's precision and may alias. When both are page-locked host memory the
+ * GPU can address (cudaHostGetDevicePointer succeeds; on a Grace-Blackwell
+ * node over the coherent chip-to-chip link) and the plan is periodic with
+ * d >= 2, the first pass reads host_in in place and the last pass writes
+ * host_out in place -- the data crosses the link once each way with no
+ * staging copy. Otherwise host_in is copied to a plan-owned device grid, the
+ * grid is solved and copied back.
  */
 int stencil_run_host(stencil_plan_t plan, const void* host_in, void* host_out,
                      int64_t T, void* stream);

@@ -88,7 +88,9 @@ class StencilPlan:
         return grid
 
     def run_host(self, host_in, T: int, host_out=None, stream=None):
-        """End-to-end solve of a host (CPU) tensor: H2D copy, solve, D2H copy, sync."""
+        """End-to-end solve of a host (CPU) tensor (stencil_run_host): pinned input and
+        output are read and written in place by the GPU, other buffers go through
+        a device copy; synchronises."""
         import torch
         if host_in.is_cuda or host_in.dtype != self.dtype or tuple(host_in.shape) != self.dims:
             raise ValueError("host_in must be a CPU tensor of the plan's shape and dtype")

@@ -221,7 +221,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
                           void* H, long long Mp, const int* orient, const int (*perms)[3],
                           int norient, const void* tw, int twn_log2, const double2* const* E64,
                           const float2* const* E32, int* status, cudaStream_t s,
-                          const void* const* vtabs, const void* const* vitems) {
+                          const void* const* vtabs, const void* const* vitems, R* Sout) {
     const int d = p->ndim;
     if (items < 1 || items > kMaxItems || norient < 1 || norient > kMaxOrient)
         return cudaErrorInvalidValue;
@@ -307,8 +307,10 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
             PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
         }
     }
-    PROF_LAUNCH(PASS_ROWS_C2R,
-                launch_rows_c2r<R>(H, S, Mp, n_log2, (int)rows, tw, twn_log2, status, s));
+    // d >= 2 reads S once (R2C) and writes the result once (C2R): Sout may be a
+    // different buffer, e.g. host memory the GPU maps over the chip-to-chip link
+    PROF_LAUNCH(PASS_ROWS_C2R, launch_rows_c2r<R>(H, Sout ? Sout : S, Mp, n_log2, (int)rows, tw,
+                                                  twn_log2, status, s));
     return cudaSuccess;
 }
 
@@ -329,7 +331,7 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
                                           void*, long long, const int*, const int (*)[3], int,     \
                                           const void*, int, const double2* const*,                 \
                                           const float2* const*, int*, cudaStream_t,                \
-                                          const void* const*, const void* const*);
+                                          const void* const*, const void* const*, R*);
 SFFT_SOLVE_INST(float)
 SFFT_SOLVE_INST(double)
 
@@ -478,12 +480,41 @@ int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
     return from_cuda(err);
 }
 
+// Device addresses of two host buffers that the GPU can access in place
+// (page-locked, mapped: on a Grace-Blackwell node the GPU reads and writes them
+// over the coherent chip-to-chip link), or false.
+static bool mapped_host(const void* a, const void* b, void** da, void** db) {
+    if (cudaHostGetDevicePointer(da, const_cast<void*>(a), 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(db, const_cast<void*>(b), 0) != cudaSuccess) {
+        cudaGetLastError();   // a pageable buffer: clear the error, take the copy path
+        return false;
+    }
+    return reinterpret_cast<uintptr_t>(*da) % 16 == 0 && reinterpret_cast<uintptr_t>(*db) % 16 == 0;
+}
+
 int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int64_t T,
                      void* stream) {
     if (!p || !host_in || !host_out || T < 0) return STENCIL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)p->n_cells * p->elem;
     cudaError_t err;
+    void* din = nullptr;
+    void* dout = nullptr;
+    if (p->boundary == STENCIL_PERIODIC && p->ndim >= 2 && T > 0 &&
+        mapped_host(host_in, host_out, &din, &dout)) {
+        // the R2C pass reads the input from host memory, the C2R pass writes the
+        // result there: no staging copy of either
+        if (p->precision == STENCIL_FP32)
+            err = batched_solve<float>(p, static_cast<float*>(din), p->dims, 1, T, p->H, p->Mp,
+                                       nullptr, nullptr, 1, p->tw, p->twn_log2, p->E64, p->E32,
+                                       p->status, s, nullptr, nullptr, static_cast<float*>(dout));
+        else
+            err = batched_solve<double>(p, static_cast<double*>(din), p->dims, 1, T, p->H, p->Mp,
+                                        nullptr, nullptr, 1, p->tw, p->twn_log2, p->E64, p->E32,
+                                        p->status, s, nullptr, nullptr, static_cast<double*>(dout));
+        if (err != cudaSuccess) return from_cuda(err);
+        return from_cuda(cudaStreamSynchronize(s));
+    }
     if (!p->dev_grid) {
         err = cudaMalloc(&p->dev_grid, bytes);
         if (err != cudaSuccess) {

@@ -92,7 +92,8 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
                           void* H, long long Mp, const int* orient, const int (*perms)[3],
                           int norient, const void* tw, int twn_log2, const double2* const* E64,
                           const float2* const* E32, int* status, cudaStream_t s,
-                          const void* const* vtabs, const void* const* vitems = nullptr);
+                          const void* const* vtabs, const void* const* vitems = nullptr,
+                          R* Sout = nullptr);
 template <typename R>
 cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64_t T,
                            void* H, long long Mp, const void* tw, int twn_log2,

@@ -270,3 +270,34 @@ def test_long_1d_nyquist_and_mean():
     lam_nyq = 0.7 - 0.1 - 0.2
     ref = 0.5 + lam_nyq ** T * (-1.0) ** x
     assert err_rel(run_gpu(a0, w, T, "fp64"), ref, a0) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_gemm_bf16x3"])
+@pytest.mark.parametrize("dims", [(256, 128), (32, 16, 64), (512, 256, 8)])
+def test_run_host_in_place_on_pinned_memory(precision, dims):
+    # both buffers pinned: the first and last passes address host memory directly;
+    # one pinned and one pageable: the staging-copy path. Same kernels, same bits.
+    from paper_2105_06676_gb300 import StencilPlan
+    if precision.startswith("fp32_gemm") and min(dims[:-1]) < 256:
+        pytest.skip("tensor-core variant needs strided axes >= 256")
+    T = 31
+    w = wl.weights_random_box(len(dims), 1, 12)
+    a0 = wl.grid_uniform(dims, 13)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = StencilPlan(dims, w, "periodic", precision)
+    dev = torch.tensor(a0, dtype=dt, device="cuda")
+    plan.run(dev, T)
+    torch.cuda.synchronize()
+    want = dev.cpu().numpy()
+    src = torch.tensor(a0, dtype=dt).pin_memory()
+    direct = plan.run_host(src, T, torch.empty_like(src).pin_memory())
+    staged = plan.run_host(src, T, torch.empty_like(src))
+    aliased = src.clone().pin_memory()
+    plan.run_host(aliased, T, aliased)
+    assert plan.status() == 0
+    plan.close()
+    np.testing.assert_array_equal(direct.numpy(), want)
+    np.testing.assert_array_equal(staged.numpy(), want)
+    np.testing.assert_array_equal(aliased.numpy(), want)
+    tol = 1e-10 if precision == "fp64" else 2e-4
+    assert err_rel(want, oracle.stencil_loop(a0, w, T, "periodic"), a0) <= tol
