@@ -69,6 +69,11 @@ struct stencil_plan_s {
     int* status = nullptr;
     // device grid owned by stencil_run_host
     void* dev_grid = nullptr;
+    // Lambda^T / N over the half spectrum of a periodic d >= 2 plan, cached
+    // for vt_T once a second consecutive run asks for the same T
+    void* vt = nullptr;
+    int64_t vt_T = -1;
+    int64_t last_T = -1;
     // zero-Dirichlet schedule and buffers (aperiodic.cu)
     AperiodicState* ap = nullptr;
     int64_t cutoff = 0;  // 0: automatic
