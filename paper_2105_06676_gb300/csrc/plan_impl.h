@@ -65,12 +65,13 @@ struct stencil_plan_s {
     void* H = nullptr;
     long long Mp = 0;
     size_t H_bytes = 0;
-    // latched device status (bit 0: non-finite output)
+    // latched device status (bit 0: non-finite output, bit 2: abandoned
+    // tensor-core wait)
     int* status = nullptr;
     // device grid owned by stencil_run_host
     void* dev_grid = nullptr;
-    // Lambda^T / N over the half spectrum of a periodic d >= 2 plan, cached
-    // for vt_T once a second consecutive run asks for the same T
+    // Lambda^T / N over the half spectrum of a periodic 3-D plan, cached for
+    // vt_T once a second consecutive run asks for the same T
     void* vt = nullptr;
     int64_t vt_T = -1;
     int64_t last_T = -1;
