@@ -239,8 +239,12 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     cudaError_t err;
     if (d == 1) {
         // every item of a 1-D batch has the one orientation
-        if (n > 16 * (sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64)) {
-            // longer than one CTA holds: n = n1 x n2 passes; Lambda^T per element
+        // n1 x n2 passes when one CTA cannot hold the row, and for a single FP64
+        // row of >= 512 points: one CTA would leave every other SM's FP64 units
+        // idle (4096-point FP64 heat solve 0.155 ms in one CTA)
+        const bool spread = items == 1 && sizeof(R) == 8 && n_log2 >= 9 && !vitems;
+        if (n > 16 * (sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64) || spread) {
+            // n = n1 x n2 passes; Lambda^T per element
             if (vitems) return cudaErrorInvalidValue;
             const int n2_log2 = std::min(11, (n_log2 + 1) / 2);   // two rows per 256-thread CTA
             PROF_LAUNCH(PASS_FUSED_1D,
@@ -249,9 +253,11 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
             return cudaSuccess;
         }
         RowTables rt;
-        for (int i = 0; i < kMaxItems; ++i) rt.t[i] = ss.vtab_item[i];
+        for (int i = 0; i < kMaxItems; ++i)
+            rt.t[i] = ss.vtab_item[i] ? ss.vtab_item[i] : (i < items ? ss.vtab[0] : nullptr);
+        const bool tables = vitems || (vtabs && vtabs[0] && items <= kMaxItems && n >= 16);
         PROF_LAUNCH(PASS_FUSED_1D, launch_fused_1d<R>(S, n_log2, items, tw, twn_log2, ss.p[0],
-                                                      status, s, vitems ? &rt : nullptr));
+                                                      status, s, tables ? &rt : nullptr));
         return cudaSuccess;
     }
     const int64_t rows_item = d == 2 ? len[0] : len[0] * len[1];
@@ -488,16 +494,23 @@ int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
     return from_cuda(err);
 }
 
-// The multiplier table of a periodic 3-D plan (paper Sec. 4 "Step 2": the
-// symbol power is computed once per T and reused): a run evaluates Lambda^T
-// inside its fused pass, unless the previous run had the same T -- then the
-// table is built (FP64 powers, stored at pass precision) and kept for T.
-// Measured on GB300: the 3-D fused pass gains (512^3 solve 1.75 -> 1.32 ms;
-// its per-column symbol set-up is the costly part), the 2-D one loses (the
-// table's extra read outweighs the arithmetic it saves), so 2-D evaluates.
+// The multiplier table of a periodic 3-D or one-CTA 1-D plan (paper Sec. 4
+// "Step 2": the symbol power is computed once per T and reused): a run
+// evaluates Lambda^T inside its fused pass, unless the previous run had the
+// same T -- then the table is built across the whole GPU (FP64 powers,
+// stored at pass precision) and kept for T. Measured on GB300: the 3-D fused
+// pass gains (512^3 solve 1.75 -> 1.32 ms; its per-column symbol set-up is
+// the costly part), and so does a 1-D axis solved by one CTA, which otherwise
+// evaluates every FP64 power itself; the 2-D pass loses (the table's extra
+// read outweighs the arithmetic it saves), so 2-D evaluates.
 static cudaError_t periodic_table(stencil_plan_s* p, int64_t T, cudaStream_t s, const void** out) {
     *out = nullptr;
-    if (p->ndim != 3) return cudaSuccess;
+    // 1-D axes one CTA holds (their single CTA would otherwise evaluate every
+    // FP64 power itself) and 3-D
+    const bool one_cta_1d = p->ndim == 1 && p->dims[0] / 2 >= 16 &&
+                            p->dims[0] / 2 <= 16 * (p->precision == STENCIL_FP32 ? kMaxThreadsF32
+                                                                                : kMaxThreadsF64);
+    if (p->ndim != 3 && !one_cta_1d) return cudaSuccess;
     if (p->vt && p->vt_T == T) {
         *out = p->vt;
         return cudaSuccess;
@@ -505,14 +518,15 @@ static cudaError_t periodic_table(stencil_plan_s* p, int64_t T, cudaStream_t s, 
     const bool repeat = p->last_T == T;
     p->last_T = T;
     if (!repeat) return cudaSuccess;
+    const size_t vbytes = p->ndim == 1 ? (size_t)(p->dims[0] / 2 + 1) * 2 * p->elem : p->H_bytes;
     if (!p->vt) {
-        cudaError_t err = cudaMalloc(&p->vt, p->H_bytes);
+        cudaError_t err = cudaMalloc(&p->vt, vbytes);
         if (err != cudaSuccess) {
             p->vt = nullptr;
             cudaGetLastError();
             return cudaSuccess;   // no room for the table: keep evaluating in the pass
         }
-        p->dev_bytes += p->H_bytes;
+        p->dev_bytes += vbytes;
     }
     const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
     cudaError_t err = p->precision == STENCIL_FP32 ? launch_vtable<float>(p->vt, sp, p->Mp, s)

@@ -70,8 +70,8 @@ struct stencil_plan_s {
     int* status = nullptr;
     // device grid owned by stencil_run_host
     void* dev_grid = nullptr;
-    // Lambda^T / N over the half spectrum of a periodic 3-D plan, cached for
-    // vt_T once a second consecutive run asks for the same T
+    // Lambda^T / N over the half spectrum of a periodic 3-D or one-CTA 1-D
+    // plan, cached for vt_T once a second consecutive run asks for the same T
     void* vt = nullptr;
     int64_t vt_T = -1;
     int64_t last_T = -1;

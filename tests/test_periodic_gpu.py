@@ -301,3 +301,29 @@ def test_run_host_in_place_on_pinned_memory(precision, dims):
     np.testing.assert_array_equal(aliased.numpy(), want)
     tol = 1e-10 if precision == "fp64" else 2e-4
     assert err_rel(want, oracle.stencil_loop(a0, w, T, "periodic"), a0) <= tol
+
+
+@pytest.mark.parametrize("dims,precision", [((4096,), "fp64"), ((1024,), "fp32"), ((64, 32, 128), "fp32"),
+                                            ((32, 16, 64), "fp64")])
+def test_repeated_T_uses_cached_multipliers_same_result(dims, precision):
+    # the second run with the same T builds the Lambda^T table, the third reads
+    # it: every run must give the same bits, and a new T or new weights must
+    # not reuse it
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(len(dims), 1, 21)
+    a0 = wl.grid_uniform(dims, 22)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = StencilPlan(dims, w, "periodic", precision)
+    outs = []
+    for T in (37, 37, 37, 38, 37):
+        g = torch.tensor(a0, dtype=dt, device="cuda")
+        plan.run(g, T)
+        outs.append(g.cpu().numpy())
+    assert plan.status() == 0
+    plan.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[0], outs[4])
+    tol = 1e-10 if precision == "fp64" else 2e-4
+    assert err_rel(outs[3], oracle.stencil_loop(a0, w, 38, "periodic"), a0) <= tol
+    assert err_rel(outs[2], oracle.stencil_loop(a0, w, 37, "periodic"), a0) <= tol
