@@ -170,6 +170,23 @@ enum stencil_schedule {
 int stencil_plan_set_schedule(stencil_plan_t plan, int mode);
 
 /*
+ * Measured schedule choice for a zero-Dirichlet plan and one T: runs the
+ * candidates -- RecursiveBoundary with the automatic base-case cutoff, with
+ * half and with twice that cutoff (when the tiles fit), and the whole-grid
+ * loop -- three times each on a scratch copy of grid (device, prod(dims)
+ * elements, not modified), times the last run of each with CUDA events on
+ * stream, and keeps the fastest for later runs of this T while the plan's
+ * schedule is STENCIL_SCHEDULE_AUTO with cutoff 0. Writes the times in ms to
+ * ms[i] for the first cap candidates (order: recursive, loop, recursive with
+ * half the cutoff, recursive with twice the cutoff) and returns the index of
+ * the one kept. Synchronises stream. Errors: STENCIL_EINVAL (NULL plan or
+ * grid, T < 1, cap < 0, ms NULL with cap > 0), STENCIL_EUNSUPPORTED for
+ * periodic plans (one schedule only), the status of a failing run.
+ */
+int stencil_plan_autotune(stencil_plan_t plan, const void* grid, int64_t T, void* stream,
+                          double* ms, int cap);
+
+/*
  * Per-kernel timing (measurement support, not part of the paper's method).
  * While enabled, every kernel launch of stencil_run on this plan is bracketed
  * by CUDA events recorded on the launching stream. stencil_profile_read

@@ -701,6 +701,8 @@ struct AperiodicState {
     cudaStream_t interior = nullptr;         // branch stream of the interior solve
     cudaEvent_t int_fork = nullptr, int_done = nullptr;
     std::map<int64_t, int> runs;             // eager runs so far per T
+    // schedule picked by stencil_plan_autotune per T: (mode, cutoff)
+    std::map<int64_t, std::pair<int, int64_t>> tuned;
     std::map<std::pair<int64_t, const void*>, cudaGraphExec_t> graphs;
     size_t bytes = 0;                        // device memory held (level buffers, tables, scratch)
 };
@@ -839,11 +841,11 @@ static void build_rb(const stencil_plan_s* p, Schedule& sc, int64_t T, int level
 static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb, size_t* smem,
                                             bool whole_grid = false);
 
-static int64_t auto_cutoff(const stencil_plan_s* p) {
+static int64_t auto_cutoff(const stencil_plan_s* p, int64_t cutoff) {
     // the loop's cost per leaf grows with T_b^2 while each recursion level costs
     // about three frame-sized FFT solves
     int64_t want = p->ndim == 1 ? 256 : p->ndim == 2 ? 32 : 8;
-    if (p->cutoff >= 2) want = p->cutoff;
+    if (cutoff >= 2) want = cutoff;
     // every base-case tile (output box plus the T_b-step halo) must fit in shared
     // memory: lower the cutoff until the largest leaf (T_b = cutoff - 1) fits
     while (want > 2) {
@@ -1243,11 +1245,18 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
     auto it = st->schedules.find(T);
     if (it == st->schedules.end()) {
         Schedule sc;
-        if (p->schedule == STENCIL_SCHEDULE_LOOP) {
+        int mode = p->schedule;
+        int64_t cut = p->cutoff;
+        auto tu = st->tuned.find(T);
+        if (mode == STENCIL_SCHEDULE_AUTO && cut == 0 && tu != st->tuned.end()) {
+            mode = tu->second.first;     // measured by stencil_plan_autotune
+            cut = tu->second.second;
+        }
+        if (mode == STENCIL_SCHEDULE_LOOP) {
             build_loop(p, sc, T);
         } else {
-            build_rb(p, sc, T, 0, auto_cutoff(p));
-            if (p->schedule == STENCIL_SCHEDULE_AUTO && p->cutoff == 0) {
+            build_rb(p, sc, T, 0, auto_cutoff(p, cut));
+            if (mode == STENCIL_SCHEDULE_AUTO && cut == 0) {
                 // automatic mode: the plain loop when it is the cheaper schedule (a
                 // boundary region that spans the whole grid gains nothing from FFTs)
                 Schedule loop;
@@ -1495,6 +1504,65 @@ void aperiodic_forget_schedules(stencil_plan_s* p) {
 
 size_t aperiodic_bytes(const stencil_plan_s* p) { return p && p->ap ? p->ap->bytes : 0; }
 
+// Times the zero-Dirichlet schedules for T on a scratch copy of grid and keeps
+// the fastest for later runs of T (stencil_plan_autotune). Candidates:
+// RecursiveBoundary with the automatic cutoff, with half and with twice that
+// cutoff, and the whole-grid loop. Each is run three times (schedule set-up,
+// graph capture, replay); the replay is timed with events on s.
+int aperiodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStream_t s,
+                       double* ms, int cap) {
+    if (!p->ap) p->ap = new AperiodicState();
+    const int64_t c0 = auto_cutoff(p, 0);
+    std::vector<std::pair<int, int64_t>> cand = {{STENCIL_SCHEDULE_RECURSIVE, 0},
+                                                 {STENCIL_SCHEDULE_LOOP, 0}};
+    if (c0 / 2 >= 2) cand.push_back({STENCIL_SCHEDULE_RECURSIVE, c0 / 2});
+    if (auto_cutoff(p, 2 * c0) == 2 * c0) cand.push_back({STENCIL_SCHEDULE_RECURSIVE, 2 * c0});
+    const size_t bytes = (size_t)p->n_cells * p->elem;
+    void* scratch = nullptr;
+    cudaError_t err = cudaMalloc(&scratch, bytes);
+    if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? STENCIL_ENOMEM : STENCIL_ECUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_mode = p->schedule;
+    const int64_t saved_cut = p->cutoff;
+    int best = -1, rc = STENCIL_OK;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < cand.size() && rc == STENCIL_OK; ++i) {
+        p->schedule = cand[i].first;
+        p->cutoff = cand[i].second;
+        aperiodic_forget_schedules(p);
+        float t = 0.f;
+        for (int rep = 0; rep < 3 && rc == STENCIL_OK; ++rep) {
+            err = cudaMemcpyAsync(scratch, grid, bytes, cudaMemcpyDeviceToDevice, s);
+            if (err != cudaSuccess) rc = STENCIL_ECUDA;
+            if (rc == STENCIL_OK && rep == 2) cudaEventRecord(e0, s);
+            if (rc == STENCIL_OK) rc = aperiodic_run(p, scratch, T, s);
+            if (rc == STENCIL_OK && rep == 2) {
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = STENCIL_ECUDA;
+                else cudaEventElapsedTime(&t, e0, e1);
+            }
+        }
+        if (rc == STENCIL_OK) {
+            if ((int)i < cap && ms) ms[i] = t;
+            if (best < 0 || t < best_ms) {
+                best = (int)i;
+                best_ms = t;
+            }
+        }
+    }
+    p->schedule = saved_mode;
+    p->cutoff = saved_cut;
+    aperiodic_forget_schedules(p);
+    if (rc == STENCIL_OK) p->ap->tuned[T] = cand[best];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    return rc == STENCIL_OK ? best : rc;
+}
+
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s) {
     cudaError_t err = p->precision == STENCIL_FP32
                           ? aperiodic_impl<float>(p, static_cast<float*>(grid), T, s)
@@ -1550,7 +1618,7 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
     p.nweights = 1;
     for (int a = 0; a < ndim; ++a) p.nweights *= 2 * radius + 1;
     Schedule sc;
-    build_rb(&p, sc, T, 0, auto_cutoff(&p));
+    build_rb(&p, sc, T, 0, auto_cutoff(&p, p.cutoff));
     if (cutoff == 0) {
         Schedule loop;
         const double c_loop = build_loop(&p, loop, T);

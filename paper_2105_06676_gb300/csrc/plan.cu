@@ -652,6 +652,13 @@ extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     return STENCIL_OK;
 }
 
+extern "C" int stencil_plan_autotune(stencil_plan_t p, const void* grid, int64_t T, void* stream,
+                                     double* ms, int cap) {
+    if (!p || !grid || T < 1 || cap < 0 || (cap > 0 && !ms)) return STENCIL_EINVAL;
+    if (p->boundary != STENCIL_ZERO_DIRICHLET) return STENCIL_EUNSUPPORTED;
+    return aperiodic_autotune(p, grid, T, static_cast<cudaStream_t>(stream), ms, cap);
+}
+
 extern "C" int stencil_plan_set_schedule(stencil_plan_t p, int mode) {
     if (!p || mode < STENCIL_SCHEDULE_AUTO || mode > STENCIL_SCHEDULE_LOOP) return STENCIL_EINVAL;
     if (p->schedule != mode) aperiodic_forget_schedules(p);

@@ -108,6 +108,10 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
 }  // namespace sfft
 
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
+// Measures the schedule candidates for T and keeps the fastest; returns its
+// index (times in ms[i] for i < cap) or a negative status.
+int aperiodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStream_t s,
+                       double* ms, int cap);
 void aperiodic_release(stencil_plan_s* p);
 // drop captured graphs (their kernel parameters hold the plan's weights)
 void aperiodic_forget_graphs(stencil_plan_s* p);

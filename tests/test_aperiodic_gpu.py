@@ -247,3 +247,29 @@ def test_3d_radius3_recursion_matches_loop(dims, T, precision):
     assert plan.status() == 0
     plan.close()
     assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("dims,r,T", [((256, 256), 1, 300), ((64, 64, 32), 2, 20), ((4096,), 2, 500)])
+def test_autotune_keeps_fastest_and_stays_exact(dims, r, T):
+    from paper_2105_06676_gb300 import StencilPlan, StencilError
+    w = wl.weights_random_box(len(dims), r, 70 + T)
+    a0 = wl.grid_uniform(dims, 71 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    plan = StencilPlan(dims, w, "dirichlet", "fp32")
+    g = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    res = plan.autotune(g, T)
+    torch.cuda.synchronize()
+    assert np.array_equal(g.cpu().numpy(), a0.astype(np.float32))    # input untouched
+    times = res["ms"]
+    assert res["chosen"] in times and times[res["chosen"]] == min(times.values())
+    assert {"recursive", "loop"} <= set(times)
+    for _ in range(2):
+        g.copy_(torch.tensor(a0, dtype=torch.float32))
+        plan.run(g, T)
+        assert plan.status() == 0
+        assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4
+    plan.close()
+    per = StencilPlan(dims, w, "periodic", "fp32")
+    with pytest.raises(StencilError):
+        per.autotune(g, T)
+    per.close()

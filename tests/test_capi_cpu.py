@@ -113,6 +113,7 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.stencil_symbol_power(None, 1, None, None) == -1
     assert lib.stencil_plan_set_cutoff(None, 8) == -1
     assert lib.stencil_plan_set_schedule(None, 0) == -1
+    assert lib.stencil_plan_autotune(None, None, 5, None, None, 0) == -1
     assert lib.stencil_profile_enable(None, 1) == -1
 
 
