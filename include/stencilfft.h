@@ -156,30 +156,36 @@ int stencil_plan_set_cutoff(stencil_plan_t plan, int64_t cutoff);
  * paper Sec. 5, or the direct loop of Sec. 1 "Problem Specification" when a
  * cost estimate of the boundary region says it is cheaper -- a region that
  * covers most of the grid gains nothing from FFTs), STENCIL_SCHEDULE_RECURSIVE
- * (always RecursiveBoundary) or STENCIL_SCHEDULE_LOOP (always the temporally
- * blocked direct loop over the whole grid). The result does not depend on it
- * beyond rounding. Changing it or the cutoff drops the plan's cached
+ * (always RecursiveBoundary), STENCIL_SCHEDULE_LOOP (always the temporally
+ * blocked direct loop over the whole grid) or STENCIL_SCHEDULE_CLUSTER (the
+ * direct loop with the whole grid held in the distributed shared memory of
+ * one thread-block cluster, one launch for all T steps; a later
+ * stencil_run returns STENCIL_EUNSUPPORTED when the grid does not fit). The
+ * result does not depend on it beyond rounding. Changing it or the cutoff drops the plan's cached
  * schedules and graphs (waits for the device). Returns STENCIL_EINVAL for a
  * NULL plan or an unknown mode.
  */
 enum stencil_schedule {
     STENCIL_SCHEDULE_AUTO = 0,
     STENCIL_SCHEDULE_RECURSIVE = 1,
-    STENCIL_SCHEDULE_LOOP = 2
+    STENCIL_SCHEDULE_LOOP = 2,
+    STENCIL_SCHEDULE_CLUSTER = 3
 };
 int stencil_plan_set_schedule(stencil_plan_t plan, int mode);
 
 /*
  * Measured schedule choice for a zero-Dirichlet plan and one T: runs the
  * candidates -- RecursiveBoundary with the automatic base-case cutoff, with
- * half and with twice that cutoff (when the tiles fit), and the whole-grid
- * loop -- three times each on a scratch copy of grid (device, prod(dims)
+ * half and with twice that cutoff (when the tiles fit), the whole-grid loop
+ * and, when the grid fits one cluster, the cluster-resident loop -- three
+ * times each on a scratch copy of grid (device, prod(dims)
  * elements, not modified), times the last run of each with CUDA events on
  * stream, and keeps the fastest for later runs of this T while the plan's
  * schedule is STENCIL_SCHEDULE_AUTO with cutoff 0. Writes the times in ms to
- * ms[i] for the first cap candidates (order: recursive, loop, recursive with
- * half the cutoff, recursive with twice the cutoff) and returns the index of
- * the one kept. Synchronises stream. Errors: STENCIL_EINVAL (NULL plan or
+ * ms[i] for the first cap of five fixed slots -- 0 recursive, 1 loop,
+ * 2 recursive with half the cutoff, 3 recursive with twice the cutoff,
+ * 4 cluster-resident loop; -1 for a slot that does not apply -- and returns
+ * the slot of the one kept. Synchronises stream. Errors: STENCIL_EINVAL (NULL plan or
  * grid, T < 1, cap < 0, ms NULL with cap > 0), STENCIL_EUNSUPPORTED for
  * periodic plans (one schedule only), the status of a failing run.
  */
@@ -213,8 +219,11 @@ const char* stencil_profile_kind_name(int kind);
  *                                      -- base case over output tiles
  *   4, T_c                             -- T_c steps of the loop on the whole grid
  *   5, T                               -- T single steps of the loop on the whole grid
+ *   6, T                               -- T steps of the loop on the whole grid held
+ *                                         in one thread-block cluster's shared memory
+ *                                         (only where a GPU that can run it is present)
  * With cutoff 0 the schedule is the one the solver runs: RecursiveBoundary, or
- * the plain loop (records 4 / 5 only) when its estimated cost is lower.
+ * the plain loop (records 4 / 5 / 6 only) when its estimated cost is lower.
  * Axes beyond ndim are reported with extent 1. A strip's box cell q maps to
  * grid cell off + q when q < valid on every axis; a scatter writes the cells
  * with lo < dist <= hi and, when face_axis >= 0, distance to that face <= hi.

@@ -74,8 +74,8 @@ class StencilPlan:
     def autotune(self, grid, T: int, stream=None) -> dict:
         """Time the zero-Dirichlet schedules for T on a copy of `grid` (CUDA tensor,
         unchanged) and keep the fastest (stencil_plan_autotune)."""
-        names = ["recursive", "loop", "recursive_half_cutoff", "recursive_double_cutoff"]
-        ms = (ctypes.c_double * len(names))(*([-1.0] * len(names)))
+        names = ["recursive", "loop", "recursive_half_cutoff", "recursive_double_cutoff", "cluster"]
+        ms = (ctypes.c_double * len(names))()
         rc = _capi.lib().stencil_plan_autotune(self._handle, ctypes.c_void_p(grid.data_ptr()), int(T),
                                                _stream_ptr(stream), ms, len(names))
         if rc < 0:
@@ -83,8 +83,9 @@ class StencilPlan:
         return {"chosen": names[rc], "ms": {n: ms[i] for i, n in enumerate(names) if ms[i] >= 0}}
 
     def set_schedule(self, mode: str) -> None:
-        """Zero-Dirichlet schedule: "auto", "recursive" or "loop" (stencil_plan_set_schedule)."""
-        code = {"auto": 0, "recursive": 1, "loop": 2}[mode]
+        """Zero-Dirichlet schedule: "auto", "recursive", "loop" or "cluster"
+        (stencil_plan_set_schedule)."""
+        code = {"auto": 0, "recursive": 1, "loop": 2, "cluster": 3}[mode]
         _capi.check(_capi.lib().stencil_plan_set_schedule(self._handle, code),
                     "stencil_plan_set_schedule")
 

@@ -43,6 +43,7 @@
 // branch stream and rejoin the main stream before the scatter that consumes
 // them. From the second run for a given T and grid the whole schedule is
 // replayed as one CUDA graph captured from those streams.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -534,6 +535,145 @@ k_step_3d_stream(const R* __restrict__ A, R* __restrict__ B, const __grid_consta
     }
 }
 
+// The whole loop (paper Sec. 1 "Problem Specification", zero ghosts) for a
+// grid small enough to live in the shared memory of one thread-block cluster:
+// CTA `rank` keeps planes [rank S, (rank + 1) S) of axis 0 plus r ghost planes
+// on each side, every plane padded with a zero ring of width r, in two
+// buffers. Each step computes the CTA's own planes from `cur` into `nxt`
+// (axis-0 register window as in k_step_3d_stream), pushes its first and last
+// r planes into the neighbours' `nxt` ghost planes through distributed shared
+// memory, and meets the cluster at one barrier; the grid is read once at the
+// start and written once at the end. Ghost planes beyond the grid and the
+// rings are never written, so they stay zero.
+namespace cgx = cooperative_groups;
+
+constexpr int kClusterThreads = 512;
+
+struct ClusterGeom {
+    int S;          // own planes (axis 0) per CTA
+    int L1p, L2p;   // padded plane extents (1 for absent axes)
+    int P;          // elements per padded plane
+    int Q;          // interior cells per plane
+    int G;          // axis-0 groups of threads per CTA
+};
+
+struct ClusterPlan {
+    bool ok = false;
+    int cs = 0;        // CTAs in the cluster
+    ClusterGeom g{};
+    size_t smem = 0;   // dynamic shared memory per CTA
+};
+
+constexpr int kClusterSmemMax = 226 * 1024;
+
+template <typename R, int RAD, int D>
+__global__ void __launch_bounds__(kClusterThreads)
+k_loop_cluster(R* __restrict__ grid, const __grid_constant__ BaseParams p,
+               const __grid_constant__ ClusterGeom cg, long long T) {
+    constexpr int W = 2 * RAD + 1;
+    constexpr int RY = D >= 2 ? RAD : 0, RX = D == 3 ? RAD : 0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cgx::cluster_group cluster = cgx::this_cluster();
+    const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
+    const int planes = cg.S + 2 * RAD;
+    const int bufsz = planes * cg.P;
+    R* cur = reinterpret_cast<R*>(smraw);
+    R* nxt = cur + bufsz;
+    const int L0 = p.gdims[0], L1 = D >= 2 ? p.gdims[1] : 1, L2 = D == 3 ? p.gdims[2] : 1;
+    const int z0 = rank * cg.S;   // grid plane of local plane RAD
+    for (int e = threadIdx.x; e < 2 * bufsz; e += blockDim.x) cur[e] = R(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < planes * cg.Q; e += blockDim.x) {
+        const int pl = e / cg.Q, qi = e - pl * cg.Q;
+        const int gz = z0 + pl - RAD;
+        if (gz < 0 || gz >= L0) continue;
+        const int y = qi / L2, x = qi - (qi / L2) * L2;
+        cur[pl * cg.P + (y + RY) * cg.L2p + x + RX] = grid[((long long)gz * L1 + y) * L2 + x];
+    }
+    // every CTA's buffers are initialised before any neighbour pushes into them
+    cluster.sync();
+    for (long long t = 0; t < T; ++t) {
+        for (int item = threadIdx.x; item < cg.G * cg.Q; item += blockDim.x) {
+            const int g = item / cg.Q, qi = item - g * cg.Q;
+            const int za = g * cg.S / cg.G, zb = (g + 1) * cg.S / cg.G;
+            const int y = qi / L2, x = qi - (qi / L2) * L2;
+            const int c0 = (y + RY) * cg.L2p + x + RX;
+            R acc[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) acc[i] = R(0);
+            // output plane o (local) takes input planes o - r .. o + r; while
+            // input plane pl is added, acc[i] is output plane pl - r + i, and
+            // after it acc[0] (plane pl - r) is complete
+            for (int pl = za; pl < zb + 2 * RAD; ++pl) {
+                const R* src = cur + pl * cg.P + c0;
+                if constexpr (D == 3) {
+                    R nb[W][W];
+#pragma unroll
+                    for (int m1 = 0; m1 < W; ++m1)
+#pragma unroll
+                        for (int m2 = 0; m2 < W; ++m2) nb[m1][m2] = src[(m1 - RAD) * cg.L2p + m2 - RAD];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        R sacc = 0;
+#pragma unroll
+                        for (int m1 = 0; m1 < W; ++m1)
+#pragma unroll
+                            for (int m2 = 0; m2 < W; ++m2)
+                                sacc += base_weight<R>(p, ((W - 1 - i) * W + m1) * W + m2) * nb[m1][m2];
+                        acc[i] += sacc;
+                    }
+                } else if constexpr (D == 2) {
+                    R nb[W];
+#pragma unroll
+                    for (int m1 = 0; m1 < W; ++m1) nb[m1] = src[m1 - RAD];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        R sacc = 0;
+#pragma unroll
+                        for (int m1 = 0; m1 < W; ++m1)
+                            sacc += base_weight<R>(p, (W - 1 - i) * W + m1) * nb[m1];
+                        acc[i] += sacc;
+                    }
+                } else {
+                    const R v = src[0];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) acc[i] += base_weight<R>(p, W - 1 - i) * v;
+                }
+                if (pl >= za + 2 * RAD) nxt[(pl - RAD) * cg.P + c0] = acc[0];
+#pragma unroll
+                for (int i = 0; i + 1 < W; ++i) acc[i] = acc[i + 1];
+                acc[W - 1] = R(0);
+            }
+        }
+        __syncthreads();
+        // own first r planes -> lower neighbour's upper ghosts, own last r
+        // planes -> upper neighbour's lower ghosts
+        if (RAD > 0) {
+            const int span = RAD * cg.P;
+            if (rank > 0) {
+                R* dst = cluster.map_shared_rank(nxt, rank - 1) + (cg.S + RAD) * cg.P;
+                const R* srcp = nxt + RAD * cg.P;
+                for (int e = threadIdx.x; e < span; e += blockDim.x) dst[e] = srcp[e];
+            }
+            if (rank + 1 < nrank) {
+                R* dst = cluster.map_shared_rank(nxt, rank + 1);
+                const R* srcp = nxt + cg.S * cg.P;
+                for (int e = threadIdx.x; e < span; e += blockDim.x) dst[e] = srcp[e];
+            }
+        }
+        cluster.sync();
+        R* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    for (int e = threadIdx.x; e < cg.S * cg.Q; e += blockDim.x) {
+        const int pl = e / cg.Q, qi = e - pl * cg.Q;
+        const int y = qi / L2, x = qi - (qi / L2) * L2;
+        grid[((long long)(z0 + pl) * L1 + y) * L2 + x] =
+            cur[(pl + RAD) * cg.P + (y + RY) * cg.L2p + x + RX];
+    }
+}
+
 // 2-D gather and scatter of batch items in 32 x 32 tiles of the box. A
 // transposed item (perm = (1, 0)) goes through a shared tile so that both the
 // grid side and the box side are accessed along their contiguous axis.
@@ -664,8 +804,9 @@ struct Op {
     // SOLVE / SCATTER: a periodic strip solve and its write-back (step index);
     // BASE: a RecursiveBoundary leaf, T steps of the loop on the frame;
     // LOOP: T steps of the loop on the whole grid (temporally blocked tiles);
-    // STEP: T single-step launches of the loop on the whole grid (3-D)
-    enum Kind { SOLVE, SCATTER, BASE, LOOP, STEP } kind;
+    // STEP: T single-step launches of the loop on the whole grid (3-D);
+    // CLUSTER: T steps of the loop in one thread-block cluster's shared memory
+    enum Kind { SOLVE, SCATTER, BASE, LOOP, STEP, CLUSTER } kind;
     int step;
     int64_t T;
 };
@@ -681,6 +822,7 @@ struct Schedule {
     std::vector<Op> ops;
     std::vector<VTable> tables;
     bool loop = false;         // the plain loop over the whole grid (no interior solve)
+    ClusterPlan cluster;       // launch shape of an Op::CLUSTER
 };
 
 struct LevelBuffers {
@@ -1151,7 +1293,7 @@ static double stencil_points(const stencil_plan_s* p) { return (double)p->nweigh
 // Cells (output tile plus halo) of a list of tiles, and the time-setting
 // equivalent: the total, or the largest tile times the concurrent slots.
 static double tile_cells_effective(const stencil_plan_s* p, const std::vector<BaseTile>& tiles,
-                                   int64_t halo) {
+                                   int64_t halo, bool whole_grid = false) {
     double total = 0.0, largest = 0.0;
     for (const BaseTile& t : tiles) {
         double v = 1.0;
@@ -1161,9 +1303,12 @@ static double tile_cells_effective(const stencil_plan_s* p, const std::vector<Ba
         total += v;
         largest = std::max(largest, v);
     }
-    // calibrated on 3-D frames (tens of tiles); 2-D frames measured close to
+    // calibrated on 3-D frames (tens of tiles) and on launches of a few tiles
+    // over small 1-D / 2-D grids; 2-D frames of many tiles measured close to
     // their total work
-    return p->ndim == 3 ? std::max(total, largest * kTileSlots) : total;
+    (void)whole_grid;
+    const bool idle = p->ndim == 3 || tiles.size() < 38;
+    return idle ? std::max(total, largest * kTileSlots) : total;
 }
 
 static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t T) {
@@ -1171,9 +1316,12 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
     int64_t maxdist = p->dims[0] / 2;
     for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
     if (p->radius * T < maxdist) c += (double)p->n_cells * fft_cell_s(p);   // interior solve
+    // a strip batch: gather, three or five FFT passes, table and scatter
+    // launches and the step's stream joins -- about 100 us of fixed cost per
+    // batch measured on small grids (128 x 512, 4096 batches: 1.0 s)
     for (const Step& st : sc.steps)
         for (const Batch& b : st.batches)
-            c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + 6 * kLaunchS;
+            c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + 1e-4;
     // base leaves repeat a few T_b values thousands of times: price each once
     std::map<int64_t, double> leaf;
     for (const Op& op : sc.ops) {
@@ -1191,9 +1339,169 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
     return c;
 }
 
-// The plain loop as a schedule: whole-grid blocked tiles of Tc steps (1-D,
-// 2-D) or single steps (3-D); returns its estimated cost.
+// Launch shape of k_loop_cluster for the plan's grid: the largest cluster
+// (16, else 8, 4, 2 CTAs) whose slabs hold at least r planes, whose two
+// buffers fit one CTA's shared memory and that the device can run.
+
+template <typename R, int RAD, int D>
+static const void* cluster_kernel() {
+    return reinterpret_cast<const void*>(k_loop_cluster<R, RAD, D>);
+}
+
+template <typename R>
+static const void* cluster_kernel_for(int radius, int ndim) {
+#define SFFT_CK(RADV)                                                               \
+    case RADV:                                                                     \
+        return ndim == 1 ? cluster_kernel<R, RADV, 1>()                            \
+               : ndim == 2 ? cluster_kernel<R, RADV, 2>() : cluster_kernel<R, RADV, 3>();
+    switch (radius) {
+        SFFT_CK(0)
+        SFFT_CK(1)
+        SFFT_CK(2)
+        SFFT_CK(3)
+        default: return nullptr;
+    }
+#undef SFFT_CK
+}
+
+static bool have_device() {
+    static const bool yes = [] {
+        int n = 0;
+        const bool ok = cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
+        cudaGetLastError();
+        return ok;
+    }();
+    return yes;
+}
+
+static ClusterPlan plan_cluster(const stencil_plan_s* p) {
+    ClusterPlan cp;
+    if (!have_device()) return cp;
+    const int d = p->ndim, r = p->radius;
+    const int64_t L0 = p->dims[0];
+    const void* kern = p->precision == STENCIL_FP32 ? cluster_kernel_for<float>(r, d)
+                                                    : cluster_kernel_for<double>(r, d);
+    if (!kern) return cp;
+    for (int cs = 16; cs >= 2; cs /= 2) {
+        if (L0 % cs != 0 || L0 / cs < std::max(r, 1)) continue;
+        ClusterGeom g;
+        g.S = (int)(L0 / cs);
+        g.L1p = d >= 2 ? (int)p->dims[1] + 2 * r : 1;
+        g.L2p = d == 3 ? (int)p->dims[2] + 2 * r : 1;
+        g.P = g.L1p * g.L2p;
+        g.Q = (int)((d >= 2 ? p->dims[1] : 1) * (d == 3 ? p->dims[2] : 1));
+        g.G = std::max(1, std::min(g.S, kClusterThreads / g.Q));
+        const size_t smem = 2 * (size_t)(g.S + 2 * r) * g.P * p->elem;
+        if (smem > (size_t)kClusterSmemMax) continue;
+        // the device must be able to run the cluster (fails without a GPU)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                           cudaSuccess)) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs, 1, 1);
+        cfg.blockDim = dim3(kClusterThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        cp.ok = true;
+        cp.cs = cs;
+        cp.g = g;
+        cp.smem = smem;
+        return cp;
+    }
+    return cp;
+}
+
+template <typename R>
+static cudaError_t launch_cluster(stencil_plan_s* p, const ClusterPlan& cp, R* X, int64_t T,
+                                  cudaStream_t s) {
+    BaseParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.ndim = p->ndim;
+    for (int a = 0; a < p->ndim; ++a) bp.gdims[a] = (int)p->dims[a];
+    for (int i = 0; i < p->nweights; ++i) {
+        bp.w[i] = p->weights[i];
+        bp.wf[i] = (float)p->weights[i];
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cp.cs, 1, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = cp.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cp.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const long long TT = (long long)T;
+    cudaError_t err = cudaSuccess;
+    p->prof.begin(PASS_BASE_LOOP, s);
+#define SFFT_CL(RADV, DV)                                                                 \
+    err = cudaLaunchKernelEx(&cfg, k_loop_cluster<R, RADV, DV>, X, bp, cp.g, TT)
+#define SFFT_CL_D(RADV)                                                                   \
+    case RADV:                                                                           \
+        if (p->ndim == 1) SFFT_CL(RADV, 1);                                              \
+        else if (p->ndim == 2) SFFT_CL(RADV, 2);                                         \
+        else SFFT_CL(RADV, 3);                                                           \
+        break;
+    switch (p->radius) {
+        SFFT_CL_D(0)
+        SFFT_CL_D(1)
+        SFFT_CL_D(2)
+        SFFT_CL_D(3)
+        default: err = cudaErrorInvalidValue;
+    }
+#undef SFFT_CL_D
+#undef SFFT_CL
+    p->prof.end(s);
+    return err;
+}
+
+// The plain loop as a schedule: the cluster-resident loop when the grid fits
+// one cluster and its estimate is lower, else whole-grid blocked tiles of Tc
+// steps (1-D, 2-D) or single steps (3-D); returns its estimated cost.
+static double build_loop_tiles(const stencil_plan_s* p, Schedule& sc, int64_t T);
+
 static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
+    Schedule tiles;
+    const double c_tiles = build_loop_tiles(p, tiles, T);
+    // 1-D grids: the tiled loop measured faster (it spreads over every SM)
+    const ClusterPlan cp = p->ndim >= 2 ? plan_cluster(p) : ClusterPlan{};
+    if (cp.ok) {
+        // per step (GB300 fit over 2-D and 3-D grids of 4K-262K cells): about
+        // 1 us of push and cluster barrier plus the CTA's share of the point
+        // updates at 1.2e11 (FP32) / 6e8 (FP64) per second per SM
+        const double rate = p->precision == STENCIL_FP32 ? 1.2e11 : 6e8;
+        const double step = (double)p->n_cells * stencil_points(p) / (cp.cs * rate) + 1.05e-6;
+        const double c_cluster = (double)T * step + 2 * kLaunchS;
+        if (c_cluster < c_tiles) {
+            sc.loop = true;
+            sc.cluster = cp;
+            sc.ops.push_back(Op{Op::CLUSTER, -1, T});
+            return c_cluster;
+        }
+    }
+    sc = std::move(tiles);
+    return c_tiles;
+}
+
+static double build_loop_tiles(const stencil_plan_s* p, Schedule& sc, int64_t T) {
     sc.loop = true;
     if (p->ndim == 3) {
         // axis-0 streamed steps: FMA-bound at about 8e12 (FP32) / 3.6e11 (FP64)
@@ -1210,7 +1518,7 @@ static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
         size_t smem = 0;
         const std::vector<BaseTile> tiles = make_base_tiles(p, tc, &smem, true);
         if (smem > (size_t)kSmemBudget) break;
-        const double cells = tile_cells_effective(p, tiles, p->radius * tc);
+        const double cells = tile_cells_effective(p, tiles, p->radius * tc, true);
         const double cost = cells * (double)T * stencil_points(p) * loop_point_s(p) +
                             (double)(T / tc + 1) * 2 * kLaunchS;
         if (best < 0 || cost < best) {
@@ -1252,7 +1560,12 @@ static cudaError_t prepare(stencil_plan_s* p, int64_t T, Schedule** out) {
             mode = tu->second.first;     // measured by stencil_plan_autotune
             cut = tu->second.second;
         }
-        if (mode == STENCIL_SCHEDULE_LOOP) {
+        if (mode == STENCIL_SCHEDULE_CLUSTER) {
+            sc.cluster = plan_cluster(p);
+            if (!sc.cluster.ok) return cudaErrorInvalidValue;   // grid too large for one cluster
+            sc.loop = true;
+            sc.ops.push_back(Op{Op::CLUSTER, -1, T});
+        } else if (mode == STENCIL_SCHEDULE_LOOP) {
             build_loop(p, sc, T);
         } else {
             build_rb(p, sc, T, 0, auto_cutoff(p, cut));
@@ -1349,6 +1662,12 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
         }
         if (op.kind == Op::STEP) {
             err = launch_steps<R>(p, X, static_cast<R*>(st->Y), op.T, main);
+            if (err != cudaSuccess) return err;
+            continue;
+        }
+        if (op.kind == Op::CLUSTER) {
+            if (!sc.cluster.ok) return cudaErrorInvalidValue;
+            err = launch_cluster<R>(p, sc.cluster, X, op.T, main);
             if (err != cudaSuccess) return err;
             continue;
         }
@@ -1505,18 +1824,23 @@ void aperiodic_forget_schedules(stencil_plan_s* p) {
 size_t aperiodic_bytes(const stencil_plan_s* p) { return p && p->ap ? p->ap->bytes : 0; }
 
 // Times the zero-Dirichlet schedules for T on a scratch copy of grid and keeps
-// the fastest for later runs of T (stencil_plan_autotune). Candidates:
-// RecursiveBoundary with the automatic cutoff, with half and with twice that
-// cutoff, and the whole-grid loop. Each is run three times (schedule set-up,
-// graph capture, replay); the replay is timed with events on s.
+// the fastest for later runs of T (stencil_plan_autotune). Candidates, in
+// fixed slots: RecursiveBoundary with the automatic cutoff, the whole-grid
+// loop, RecursiveBoundary with half and with twice that cutoff, the
+// cluster-resident loop. Each is run three times (schedule set-up, graph
+// capture, replay); the replay is timed with events on s.
 int aperiodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStream_t s,
                        double* ms, int cap) {
     if (!p->ap) p->ap = new AperiodicState();
+    // fixed slots; a slot that does not apply keeps mode -1 and time -1
     const int64_t c0 = auto_cutoff(p, 0);
     std::vector<std::pair<int, int64_t>> cand = {{STENCIL_SCHEDULE_RECURSIVE, 0},
-                                                 {STENCIL_SCHEDULE_LOOP, 0}};
-    if (c0 / 2 >= 2) cand.push_back({STENCIL_SCHEDULE_RECURSIVE, c0 / 2});
-    if (auto_cutoff(p, 2 * c0) == 2 * c0) cand.push_back({STENCIL_SCHEDULE_RECURSIVE, 2 * c0});
+                                                 {STENCIL_SCHEDULE_LOOP, 0},
+                                                 {-1, 0}, {-1, 0}, {-1, 0}};
+    if (c0 / 2 >= 2) cand[2] = {STENCIL_SCHEDULE_RECURSIVE, c0 / 2};
+    if (auto_cutoff(p, 2 * c0) == 2 * c0) cand[3] = {STENCIL_SCHEDULE_RECURSIVE, 2 * c0};
+    if (plan_cluster(p).ok) cand[4] = {STENCIL_SCHEDULE_CLUSTER, 0};
+    for (int i = 0; i < cap && ms; ++i) ms[i] = -1.0;
     const size_t bytes = (size_t)p->n_cells * p->elem;
     void* scratch = nullptr;
     cudaError_t err = cudaMalloc(&scratch, bytes);
@@ -1529,6 +1853,7 @@ int aperiodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStrea
     int best = -1, rc = STENCIL_OK;
     float best_ms = 0.f;
     for (size_t i = 0; i < cand.size() && rc == STENCIL_OK; ++i) {
+        if (cand[i].first < 0) continue;
         p->schedule = cand[i].first;
         p->cutoff = cand[i].second;
         aperiodic_forget_schedules(p);
@@ -1626,8 +1951,8 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
     }
     std::vector<int64_t> v;
     for (const Op& op : sc.ops) {
-        if (op.kind == Op::LOOP || op.kind == Op::STEP) {
-            v.push_back(op.kind == Op::LOOP ? 4 : 5);
+        if (op.kind == Op::LOOP || op.kind == Op::STEP || op.kind == Op::CLUSTER) {
+            v.push_back(op.kind == Op::LOOP ? 4 : op.kind == Op::STEP ? 5 : 6);
             v.push_back(op.T);
             continue;
         }

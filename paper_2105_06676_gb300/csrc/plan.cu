@@ -660,7 +660,7 @@ extern "C" int stencil_plan_autotune(stencil_plan_t p, const void* grid, int64_t
 }
 
 extern "C" int stencil_plan_set_schedule(stencil_plan_t p, int mode) {
-    if (!p || mode < STENCIL_SCHEDULE_AUTO || mode > STENCIL_SCHEDULE_LOOP) return STENCIL_EINVAL;
+    if (!p || mode < STENCIL_SCHEDULE_AUTO || mode > STENCIL_SCHEDULE_CLUSTER) return STENCIL_EINVAL;
     if (p->schedule != mode) aperiodic_forget_schedules(p);
     p->schedule = mode;
     return STENCIL_OK;

@@ -273,3 +273,36 @@ def test_autotune_keeps_fastest_and_stays_exact(dims, r, T):
     with pytest.raises(StencilError):
         per.autotune(g, T)
     per.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dims,r,T", [((64, 64), 2, 500), ((32, 16, 16), 1, 200), ((4096,), 3, 700),
+                                      ((128, 32), 1, 301), ((16, 8, 32), 3, 40), ((256, 256), 1, 1000)])
+def test_cluster_resident_loop_matches_loop(dims, r, T, precision):
+    # small grids with long T: the whole loop inside one thread-block cluster
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(len(dims), r, 80 + T)
+    a0 = wl.grid_uniform(dims, 81 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(dims, w, "dirichlet", precision)
+    plan.set_schedule("cluster")
+    for _ in range(3):                        # eager, capture, replay
+        g.copy_(torch.tensor(a0, dtype=dt))
+        plan.run(g, T)
+        assert plan.status() == 0
+        assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
+    plan.close()
+
+
+
+
+def test_cluster_schedule_rejects_grids_too_large():
+    from paper_2105_06676_gb300 import StencilPlan, StencilError
+    plan = StencilPlan((1024, 1024), wl.weights_random_box(2, 1, 3), "dirichlet", "fp32")
+    plan.set_schedule("cluster")
+    g = torch.rand((1024, 1024), dtype=torch.float32, device="cuda")
+    with pytest.raises(StencilError):
+        plan.run(g, 10)
+    plan.close()

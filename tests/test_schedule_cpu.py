@@ -53,7 +53,7 @@ def decode(v):
         elif kind == 2:
             ops.append(("scatter", v[i + 1]))
             i += 2
-        elif kind in (4, 5):
+        elif kind in (4, 5, 6):
             ops.append(("loop", v[i + 1]))
             i += 2
         elif kind == 3:
