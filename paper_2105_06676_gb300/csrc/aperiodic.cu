@@ -689,6 +689,14 @@ k_copy_2d(R* __restrict__ X, R* __restrict__ S, const __grid_constant__ BatchGeo
     const int q0b = blockIdx.y * 32, q1b = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const bool transposed = it.perm[0] == 1;
+    if (SCATTER && it.face_axis >= 0) {
+        // kept cells have face distance in (lo, hi]; the face normal is box
+        // axis 0, so only box rows in that band can be written
+        const int a = it.face_axis, offn = it.off[a], Ln = a == 0 ? L0 : L1;
+        const int klo = it.face_side == 0 ? b.lo - offn : Ln - offn - b.hi;
+        const int khi = it.face_side == 0 ? b.hi - offn : Ln - offn - b.lo;
+        if (q0b >= khi || q0b + 32 <= klo) return;
+    }
     auto keep = [&](int g0, int g1) {
         const int d = min(min(g0 + 1, L0 - g0), min(g1 + 1, L1 - g1));
         if (d <= b.lo || d > b.hi) return false;
@@ -985,8 +993,10 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
 
 static int64_t auto_cutoff(const stencil_plan_s* p, int64_t cutoff) {
     // the loop's cost per leaf grows with T_b^2 while each recursion level costs
-    // about three frame-sized FFT solves
-    int64_t want = p->ndim == 1 ? 256 : p->ndim == 2 ? 32 : 8;
+    // about eight grid-sized FFT solves (four face strips of width 2 sigma T_k
+    // per node, two solves per node); 2-D: 64 measured best on 8192^2, T = 4096
+    // (cutoff 8 / 16 / 32 / 48 / 64: 199 / 119 / 70 / 64 / 64 ms)
+    int64_t want = p->ndim == 1 ? 256 : p->ndim == 2 ? 64 : 8;
     if (cutoff >= 2) want = cutoff;
     // every base-case tile (output box plus the T_b-step halo) must fit in shared
     // memory: lower the cutoff until the largest leaf (T_b = cutoff - 1) fits
@@ -1514,7 +1524,7 @@ static double build_loop_tiles(const stencil_plan_s* p, Schedule& sc, int64_t T)
     }
     double best = -1.0;
     int64_t best_tc = 1;
-    for (int64_t tc = 1; tc <= std::min<int64_t>(T, p->ndim == 1 ? 256 : 32); tc *= 2) {
+    for (int64_t tc = 1; tc <= std::min<int64_t>(T, p->ndim == 1 ? 256 : 64); tc *= 2) {
         size_t smem = 0;
         const std::vector<BaseTile> tiles = make_base_tiles(p, tc, &smem, true);
         if (smem > (size_t)kSmemBudget) break;
