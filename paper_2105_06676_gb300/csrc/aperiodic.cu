@@ -261,6 +261,9 @@ __global__ void k_tile_copy(const R* __restrict__ Y, R* __restrict__ X,
 // walks its rows. Reads beyond the tile are the zero ring: outside the grid
 // that is the boundary condition, inside the grid it only reaches cells whose
 // values never propagate to the output box within T_b steps.
+// Rows of outputs one thread computes per item of the 2-D base case.
+constexpr int kBaseRun = 8;
+
 template <typename R, int RAD>
 __global__ void __launch_bounds__(256)
 k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict__ tiles,
@@ -291,16 +294,35 @@ k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
         const int reach = (p.Tb - step) * RAD;
         const int cy0 = max(t.lo[0] - reach, iy0) - iy0, cy1 = min(t.hi[0] + reach, iy1) - iy0;
         const int cx0 = max(t.lo[1] - reach, ix0) - ix0, cx1 = min(t.hi[1] + reach, ix1) - ix0;
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
-        for (int y = cy0 + ty; y < cy1; y += ny) {
-            for (int x = cx0 + tx; x < cx1; x += 32) {
-                const R* src = b0 + y * pitch + x;   // (y - RAD, x - RAD) in padded coordinates
-                R acc = 0;
+        // each item is a column x and a run of kBaseRun rows: the W neighbours
+        // of an input row are read once and added, slice by slice, into a
+        // window of W accumulators; while padded input row yi is added, acc[i]
+        // is output row yi - 2 RAD + i, and after it acc[0] is complete
+        const int nx = cx1 - cx0, nruns = (cy1 - cy0 + kBaseRun - 1) / kBaseRun;
+        for (int item = threadIdx.x; item < nx * nruns; item += blockDim.x) {
+            const int run = item / nx, x = cx0 + item - run * nx;
+            const int ya = cy0 + run * kBaseRun, yb = min(ya + kBaseRun, cy1);
+            R acc[W];
 #pragma unroll
-                for (int m0 = 0; m0 < W; ++m0)
+            for (int i = 0; i < W; ++i) acc[i] = R(0);
+            // padded input rows ya .. yb + 2 RAD - 1 feed outputs ya .. yb - 1
+            for (int yi = ya; yi < yb + 2 * RAD; ++yi) {
+                const R* src = b0 + yi * pitch + x;
+                R nb[W];
 #pragma unroll
-                    for (int m1 = 0; m1 < W; ++m1) acc += w[m0 * W + m1] * src[m0 * pitch + m1];
-                b1[(y + RAD) * pitch + x + RAD] = acc;
+                for (int m1 = 0; m1 < W; ++m1) nb[m1] = src[m1];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    R sacc = 0;
+#pragma unroll
+                    for (int m1 = 0; m1 < W; ++m1) sacc += w[(W - 1 - i) * W + m1] * nb[m1];
+                    acc[i] += sacc;
+                }
+                const int yo = yi - 2 * RAD;    // output row whose window closed
+                if (yo >= ya) b1[(yo + RAD) * pitch + x + RAD] = acc[0];
+#pragma unroll
+                for (int i = 0; i + 1 < W; ++i) acc[i] = acc[i + 1];
+                acc[W - 1] = R(0);
             }
         }
         __syncthreads();
