@@ -1426,8 +1426,9 @@ static ClusterPlan plan_cluster(const stencil_plan_s* p) {
         const size_t smem = 2 * (size_t)(g.S + 2 * r) * g.P * p->elem;
         if (smem > (size_t)kClusterSmemMax) continue;
         // the device must be able to run the cluster (fails without a GPU)
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
+        // (the dynamic shared-memory limit only ever rises: plans of other
+        // shapes share the kernel)
+        if ((smem > 48 * 1024 && smem_optin(kern, smem) != cudaSuccess) ||
             (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                            cudaSuccess)) {
             cudaGetLastError();
