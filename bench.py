@@ -128,6 +128,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time (the job's time) when world > 1; the tensor
+    lives where the process group's backend reduces (CUDA for NCCL)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells: int, T: int, world: int, ms: float) -> float:
+    """Whole-job point updates per second: every rank solves its own replica."""
+    return world * cells * T / (ms * 1e-3)
+
+
 def cpu_oracle_sample(w, dims, T_sample, seed):
     """Time the FP64 nested-loop oracle on T_sample steps of the full grid."""
     import oracle
@@ -344,12 +362,8 @@ def main():
     barrier()
     prof = plan32.profile_read()          # warm-up and timed launches
     plan32.profile(False)
-    ms32 = sum(times32) / len(times32)
-    if world > 1:
-        t = torch.tensor([ms32], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
-    value = world * N * T / (ms32 * 1e-3)
+    ms32 = max_over_ranks(sum(times32) / len(times32), world)
+    value = job_value(N, T, world, ms32)
     assert plan32.status() == 0
 
     # ---- FP64 path (secondary)
