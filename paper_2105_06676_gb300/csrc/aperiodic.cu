@@ -47,6 +47,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -1019,7 +1020,17 @@ static int64_t auto_cutoff(const stencil_plan_s* p, int64_t cutoff) {
     // per node, two solves per node); 2-D: 64 measured best on 8192^2, T = 4096
     // (cutoff 8 / 16 / 32 / 48 / 64: 199 / 119 / 70 / 64 / 64 ms)
     int64_t want = p->ndim == 1 ? 256 : p->ndim == 2 ? 64 : 8;
-    if (cutoff >= 2) want = cutoff;
+    if (cutoff >= 2) {
+        want = cutoff;
+    } else if (p->radius > 0) {
+        // keep each leaf's tiles at least twice the halo wide along every axis
+        // (recomputation at most (1 + 2h / extent)^d), with extent + 2h + 2r
+        // per axis fitting the shared-memory budget: h = r T_b <= (side - 2r) / 4
+        const double cells = 150.0 * 1024 / (2.0 * (double)p->elem);
+        const double side = std::pow(cells, 1.0 / p->ndim);
+        const int64_t tb = (int64_t)((side - 2.0 * p->radius) / (4.0 * p->radius));
+        want = std::max<int64_t>(2, std::min<int64_t>(want, tb + 1));
+    }
     // every base-case tile (output box plus the T_b-step halo) must fit in shared
     // memory: lower the cutoff until the largest leaf (T_b = cutoff - 1) fits
     while (want > 2) {
@@ -1349,11 +1360,15 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
     for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
     if (p->radius * T < maxdist) c += (double)p->n_cells * fft_cell_s(p);   // interior solve
     // a strip batch: gather, three or five FFT passes, table and scatter
-    // launches and the step's stream joins -- about 100 us of fixed cost per
-    // batch measured on small grids (128 x 512, 4096 batches: 1.0 s)
+    // launches and the step's stream joins, about 20 us of fixed cost (100 us
+    // for 1-D, whose strips are tiny next to it); 2-D leaves run about 5x
+    // faster than the tile-count model below says (fitted to GB300 runs of
+    // 2-D grids of 4K-67M cells, r = 1-3, and 1-D grids of 8K-16K cells)
+    const double batch_s = p->ndim == 1 ? 1e-4 : 2e-5;
     for (const Step& st : sc.steps)
         for (const Batch& b : st.batches)
-            c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + 1e-4;
+            c += (double)b.geom.items * (double)b.geom.box_cells * fft_cell_s(p) + batch_s;
+    const double leaf_scale = p->ndim == 2 ? 0.2 : 1.0;
     // base leaves repeat a few T_b values thousands of times: price each once
     std::map<int64_t, double> leaf;
     for (const Op& op : sc.ops) {
@@ -1363,7 +1378,8 @@ static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t
             size_t smem = 0;
             const std::vector<BaseTile> tiles = make_base_tiles(p, op.T, &smem);
             const double cells = tile_cells_effective(p, tiles, p->radius * op.T);
-            it = leaf.emplace(op.T, cells * (double)op.T * stencil_points(p) * loop_point_s(p) +
+            it = leaf.emplace(op.T, leaf_scale * cells * (double)op.T * stencil_points(p) *
+                                            loop_point_s(p) +
                                         2 * kLaunchS).first;
         }
         c += it->second;

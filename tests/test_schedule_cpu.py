@@ -199,8 +199,12 @@ def test_schedule_rejects_bad_arguments(lib):
 
 def test_auto_mode_picks_the_loop_when_everything_is_boundary(lib):
     # sigma T far beyond the grid: every cell feels the boundary, FFTs cannot help
-    ops = decode(fetch_schedule(lib, (64, 64), 2, 5000, 0))
+    ops = decode(fetch_schedule(lib, (16, 16), 1, 5000, 0))
     assert ops and all(o[0] == "loop" for o in ops) and sum(o[1] for o in ops) == 5000
+    # a larger grid may take base leaves over the whole grid instead (the same
+    # loop in other chunks), but never an FFT solve
+    ops = decode(fetch_schedule(lib, (32, 32), 3, 20000, 0))
+    assert ops and all(o[0] in ("loop", "base") for o in ops)
     ops = decode(fetch_schedule(lib, (16, 16, 16), 1, 300, 0))
     assert ops == [("loop", 300)]
     # the benchmark regime stays recursive
