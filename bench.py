@@ -141,6 +141,17 @@ def max_over_ranks(ms: float, world: int) -> float:
     return float(t.item())
 
 
+def fft2d_flops(dims) -> float:
+    """Flops of one 2-D periodic solve by the three-pass R2C design: rows of
+    l1/2-point complex transforms forward and back, l1/2 + 1 columns of
+    l0-point transforms forward and back, 5 n log2 n each."""
+    l0, l1 = dims
+    n = l1 // 2
+    rows = 2 * l0 * 5 * n * math.log2(n)
+    cols = 2 * (n + 1) * 5 * l0 * math.log2(l0)
+    return rows + cols
+
+
 def job_value(cells: int, T: int, world: int, ms: float) -> float:
     """Whole-job point updates per second: every rank solves its own replica."""
     return world * cells * T / (ms * 1e-3)
@@ -474,7 +485,10 @@ def main():
             "config": {"workload": WORKLOAD, "grid": list(dims), "T": T, "global_batch": world,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed (512 MiB write) between timed steps; grid restored outside the events"},
-            "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64},
+            "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64,
+                          # FP64-ALU bound: 5 n log2 n flops per complex transform
+                          "flops_per_step": fft2d_flops(dims),
+                          "tflops": fft2d_flops(dims) / (ms64 * 1e-3) / 1e12},
             "dirichlet_path": dirichlet,
             "heat1d_path": extra["heat1d_4096_fp64"],
             "star3d_path": extra["star7_3d_512_fp32"],
@@ -485,7 +499,10 @@ def main():
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
                          "per_kernel_ms": {k: round(v, 5) for k, v in avg_ms.items()},
-                         "algorithmic_bytes": algo[dominant]},
+                         "algorithmic_bytes": algo[dominant],
+                         # the whole solve (three passes) against the same peak
+                         "step_bytes": sum(algo.values()),
+                         "step_frac": sum(algo.values()) / (ms32 * 1e-3) / 1e9 / peak},
             "serving": serving,
             "gpu_launches": int(round(step_kernel_launches * args.steps)),
             "clocks": clocks,
