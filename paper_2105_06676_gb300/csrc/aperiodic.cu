@@ -1726,7 +1726,7 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
             for (const Batch& b : step.batches) {
                 const long long total = (long long)b.geom.items * b.geom.box_cells;
                 R* S = reinterpret_cast<R*>(static_cast<char*>(L.S) + b.s_off);
-                p->prof.begin(PASS_COPY, main);
+                p->prof.begin(PASS_GATHER, main);
                 if (p->ndim == 2) {
                     dim3 grid((b.geom.bdims[1] + 31) / 32, (b.geom.bdims[0] + 31) / 32, b.geom.items);
                     k_copy_2d<R, false><<<grid, 256, 0, main>>>(X, S, b.geom);
@@ -1761,7 +1761,7 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
             for (const Batch& b : step.batches) {
                 const long long total = (long long)b.geom.items * b.geom.box_cells;
                 R* S = reinterpret_cast<R*>(static_cast<char*>(L.S) + b.s_off);
-                p->prof.begin(PASS_COPY, main);
+                p->prof.begin(PASS_SCATTER, main);
                 if (p->ndim == 2) {
                     dim3 grid((b.geom.bdims[1] + 31) / 32, (b.geom.bdims[0] + 31) / 32, b.geom.items);
                     k_copy_2d<R, true><<<grid, 256, 0, main>>>(X, S, b.geom);

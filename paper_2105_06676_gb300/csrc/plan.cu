@@ -668,7 +668,7 @@ extern "C" int stencil_plan_set_schedule(stencil_plan_t p, int mode) {
 
 static const char* kPassNames[PASS_KINDS] = {
     "rows_r2c", "cols_fwd", "cols_fused", "cols_inv", "rows_c2r", "fused_1d",
-    "strip_r2c", "strip_cols", "strip_c2r", "base_loop", "copy", "vtable"};
+    "strip_r2c", "strip_cols", "strip_c2r", "base_loop", "copy", "vtable", "gather", "scatter"};
 
 extern "C" int stencil_profile_enable(stencil_plan_t p, int enable) {
     if (!p) return STENCIL_EINVAL;

@@ -24,7 +24,9 @@ enum PassKind {
     PASS_BASE_LOOP = 9,
     PASS_COPY = 10,
     PASS_VTABLE = 11,
-    PASS_KINDS = 12
+    PASS_GATHER = 12,
+    PASS_SCATTER = 13,
+    PASS_KINDS = 14
 };
 
 // Optional CUDA-event bracketing of every kernel launch of a run, on the
