@@ -266,7 +266,7 @@ __global__ void k_tile_copy(const R* __restrict__ Y, R* __restrict__ X,
 constexpr int kBaseRun = 8;
 
 template <typename R, int RAD>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict__ tiles,
           const __grid_constant__ BaseParams p) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1210,7 +1210,7 @@ static cudaError_t launch_base(stencil_plan_s* p, const BaseSet& bs, R* X, R* Y,
             if (bs.smem > 48 * 1024)                                                          \
                 err = smem_optin(reinterpret_cast<const void*>(kern), bs.smem);              \
             if (err == cudaSuccess) {                                                         \
-                kern<<<bs.count, 256, bs.smem, s>>>(X, Y, tiles, bp);                         \
+                kern<<<bs.count, p->ndim == 2 ? 512 : 256, bs.smem, s>>>(X, Y, tiles, bp);     \
                 err = cudaGetLastError();                                                     \
             }                                                                                 \
         }                                                                                     \
