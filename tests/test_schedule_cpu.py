@@ -220,3 +220,46 @@ def test_auto_loop_schedule_reproduces_dirichlet_loop(lib, dims, r, T):
     got = emulate(a0, w, T, ops)
     ref = oracle.stencil_loop(a0, w, T, "dirichlet")
     assert np.max(np.abs(got - ref)) < 1e-11
+
+
+# automatic cutoff with r = 2, 3 (bounded by the leaves' halo recomputation)
+CASES_AUTO_R = [((128, 128), 2, 40), ((256, 64), 3, 30), ((32, 32, 32), 2, 12), ((512,), 3, 200),
+                ((128, 256), 2, 75)]
+
+
+@pytest.mark.parametrize("dims,r,T", CASES_AUTO_R)
+def test_recursive_schedule_with_automatic_cutoff_reproduces_loop(lib, dims, r, T):
+    w = wl.weights_random_box(len(dims), r, 200 + T)
+    a0 = wl.grid_uniform(dims, 9 + T)
+    # cutoff 0 lets the model also pick the loop; the recursion is forced by
+    # asking for the automatic cutoff's value explicitly below
+    for cutoff in (0, auto_cutoff_value(dims, r)):
+        ops = decode(fetch_schedule(lib, dims, r, T, cutoff))
+        got = emulate(a0, w, T, ops)
+        ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(a0)) < 1e-11
+
+
+def auto_cutoff_value(dims, r, elem=4):
+    """The automatic base-case cutoff's rule restated: the largest T_b + 1 whose
+    halo h = r T_b leaves tiles at least 2h wide within the shared-memory
+    budget of 150 KB per two buffers (side of the budget's cube / square)."""
+    d = len(dims)
+    side = (150 * 1024 / (2 * elem)) ** (1.0 / d)
+    tb = int((side - 2 * r) / (4 * r))
+    return max(2, min({1: 256, 2: 64, 3: 8}[d], tb + 1))
+
+
+@pytest.mark.parametrize("dims,r,T", [((8192, 8192), 1, 4096), ((4096, 256), 2, 7004),
+                                      ((2048, 2048), 3, 500), ((512, 2048), 2, 1000),
+                                      ((64, 64, 64), 1, 40)])
+def test_automatic_cutoff_keeps_leaf_halos_small(lib, dims, r, T):
+    # every leaf of the automatic schedule satisfies 4 r T_b + 2 r <= side of
+    # the shared-memory budget, so a tile can be twice its halo wide (a cutoff
+    # chosen only by "the tile fits" gives 1-cell tiles with halos of 60+)
+    ops = decode(fetch_schedule(lib, dims, r, T, auto_cutoff_value(dims, r)))
+    leaves = [o for o in ops if o[0] == "base"]
+    assert leaves
+    side = (150 * 1024 / 8) ** (1.0 / len(dims))
+    for _, Tb, _tiles in leaves:
+        assert 4 * r * Tb + 2 * r <= side
