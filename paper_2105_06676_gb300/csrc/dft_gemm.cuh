@@ -22,8 +22,8 @@
 // to the tensor core's async proxy (fence.proxy.async) and meets the others at
 // a barrier; thread 0 issues the MMAs and commits them to an mbarrier; all
 // threads wait on it (bounded: after kSpinLimit polls the kernel records
-// kGemmTimeout in its status word and carries on with whatever is in tensor
-// memory), then load their row.
+// kGemmTimeout in its status word, waits once more with the same bound and
+// carries on with whatever is in tensor memory), then load their row.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -294,10 +294,16 @@ struct DftGemm {
             }
             mma_commit(mbar);
         }
-        const bool ok = mbar_wait(mbar, phase);
+        bool ok = mbar_wait(mbar, phase);
+        if (!ok) {
+            // record the abandoned wait, then wait once more (also bounded) so
+            // that no MMA of this stage is still running when the accumulators
+            // are read or the tensor memory is released
+            if (threadIdx.x % 32 == 0) atomicOr(status, kGemmTimeout);
+            ok = mbar_wait(mbar, phase);
+        }
         phase ^= 1;
         tc_fence_after();
-        if (!ok && threadIdx.x % 32 == 0) atomicOr(status, kGemmTimeout);
         // warp w reads lanes 32 (w % 4) .. of tile w / 4
         const uint32_t warp = threadIdx.x >> 5;
         const uint32_t taddr = tmem + ((32u * (warp & 3)) << 16) + 32u * (warp >> 2);
