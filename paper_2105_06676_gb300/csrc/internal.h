@@ -73,6 +73,16 @@ cudaError_t launch_cols_gemm(void* H, const ColGeom& g, int dir, const void* tw,
 cudaError_t launch_cols_fused_gemm(void* H, const ColGeom& g, const void* tw, int twn_log2,
                                    const SymbolSet& p, int mode, int* status, cudaStream_t s);
 
+// Persistent TMA-fed strided-axis passes for FP32 half spectra (cols_tma.cuh),
+// transform lengths 2^9..2^12: mode -1 forward, +1 inverse, 0 the fused
+// forward x V x inverse pass along axis 0 (ps required). Returns
+// cudaErrorNotSupported when the geometry or the driver does not allow it (the
+// caller then uses the register column kernels). Abandoned waits set bit 2 of
+// *status.
+bool cols_tma_ok(const void* H, const ColGeom& g);
+cudaError_t launch_cols_tma(void* H, const ColGeom& g, int mode, const void* tw, int twn_log2,
+                            const SymbolSet* ps, int* status, cudaStream_t s);
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);
 

@@ -1,0 +1,149 @@
+// Launchers of the persistent TMA-fed column passes (cols_tma.cuh) for FP32
+// half spectra: tensor-map encoding, eligibility and the kernel dispatch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "cols_tma.cuh"
+#include "internal.h"
+
+namespace sfft {
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// links only the CUDA runtime); null when the driver does not provide it.
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+int sm_count() {
+    static std::mutex mu;
+    static int count[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!count[dev]) cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev);
+    return count[dev];
+}
+
+// STENCILFFT_COLS=reg selects the register column kernels instead (A/B timing).
+bool tma_enabled() {
+    static bool on = [] {
+        const char* e = std::getenv("STENCILFFT_COLS");
+        return !(e && std::strcmp(e, "reg") == 0);
+    }();
+    return on;
+}
+
+// 5-D view of the passes' geometry: (floats of a row of columns, mid, 256 rows,
+// n/256 row blocks, outer); box = one tile.
+cudaError_t make_map(CUtensorMap* map, void* H, const ColGeom& g) {
+    const int n = 1 << g.log2n;
+    const int cpt = 1 << tma_cols_log2(g.log2n);
+    const long long srow = g.S * 8;                       // bytes between rows of the axis
+    const long long smid = g.mid > 1 ? g.ms * 8 : srow;   // unused extent-1 axis: any valid stride
+    cuuint64_t dim[5] = {(cuuint64_t)(2 * g.inner_valid), (cuuint64_t)g.mid, 256,
+                         (cuuint64_t)(n / 256), (cuuint64_t)g.outer};
+    cuuint64_t stride[4] = {(cuuint64_t)smid, (cuuint64_t)srow, (cuuint64_t)(256 * srow),
+                            (cuuint64_t)(g.outer > 1 ? g.os * 8 : (long long)n * srow)};
+    cuuint32_t box[5] = {(cuuint32_t)(2 * cpt), 1, 256, (cuuint32_t)(n / 256), 1};
+    cuuint32_t estride[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode_tiled()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, H, dim, stride, box,
+                                      estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int L, typename F>
+cudaError_t with_len(int l, F&& f) {
+    if constexpr (L > kTmaLog2Hi) {
+        return cudaErrorNotSupported;
+    } else {
+        if (l == L) return f(std::integral_constant<int, L>{});
+        return with_len<L + 1>(l, f);
+    }
+}
+
+template <int MODE, int RAD, int LOG2N>
+cudaError_t launch_t(void* H, const ColGeom& g, const CUtensorMap& map, const void* tw,
+                     int twn_log2, const SymbolSet& ps, int* status, cudaStream_t s) {
+    const size_t smem = tma_smem_bytes(LOG2N);
+    auto kern = k_cols_tma<MODE, RAD, LOG2N>;
+    cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), smem);
+    if (err != cudaSuccess) return err;
+    const int cpt = 1 << tma_cols_log2(LOG2N);
+    const int gx = (g.inner_valid + cpt - 1) / cpt;
+    const long long ntiles = (long long)gx * g.mid * g.outer;
+    const int nsm = sm_count();
+    const long long slots = 2ll * nsm;   // two CTAs per SM
+    const int grid = (int)(ntiles < slots ? ntiles : slots);
+    kern<<<grid, kTileThreads, smem, s>>>(static_cast<float2*>(H), map, g,
+                                          static_cast<const float2*>(tw), twn_log2, ps, status, gx,
+                                          (int)ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool cols_tma_ok(const void* H, const ColGeom& g) {
+    if (!tma_enabled() || !encode_tiled() || sm_count() <= 0) return false;
+    if (g.log2n < kTmaLog2Lo || g.log2n > kTmaLog2Hi) return false;
+    if (reinterpret_cast<uintptr_t>(H) % 16) return false;
+    // strides are whole 16-byte units (two FP32 complex values)
+    if ((g.S & 1) || (g.mid > 1 && (g.ms & 1)) || (g.outer > 1 && (g.os & 1))) return false;
+    const long long tiles = (long long)((g.inner_valid + (1 << tma_cols_log2(g.log2n)) - 1) >>
+                                        tma_cols_log2(g.log2n)) *
+                            g.mid * g.outer;
+    return g.inner_valid > 0 && tiles < (1ll << 31);
+}
+
+cudaError_t launch_cols_tma(void* H, const ColGeom& g, int mode, const void* tw, int twn_log2,
+                            const SymbolSet* ps, int* status, cudaStream_t s) {
+    if (!cols_tma_ok(H, g) || (mode == 0 && !ps)) return cudaErrorNotSupported;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    cudaError_t err = make_map(&map, H, g);
+    if (err != cudaSuccess) return cudaErrorNotSupported;
+    static const SymbolSet kNone = [] {
+        SymbolSet z;
+        std::memset(&z, 0, sizeof(z));
+        return z;
+    }();
+    const SymbolSet& set = ps ? *ps : kNone;
+    return with_len<kTmaLog2Lo>(g.log2n, [&](auto tag) -> cudaError_t {
+        constexpr int L = decltype(tag)::value;
+        if (mode < 0) return launch_t<-1, 0, L>(H, g, map, tw, twn_log2, set, status, s);
+        if (mode > 0) return launch_t<+1, 0, L>(H, g, map, tw, twn_log2, set, status, s);
+        switch (set.p[0].r) {
+            case 0: return launch_t<0, 0, L>(H, g, map, tw, twn_log2, set, status, s);
+            case 1: return launch_t<0, 1, L>(H, g, map, tw, twn_log2, set, status, s);
+            case 2: return launch_t<0, 2, L>(H, g, map, tw, twn_log2, set, status, s);
+            default: return launch_t<0, 3, L>(H, g, map, tw, twn_log2, set, status, s);
+        }
+    });
+}
+
+}  // namespace sfft

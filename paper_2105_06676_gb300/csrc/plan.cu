@@ -276,6 +276,8 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         if (sizeof(R) == 4 && p->gemm >= 0)
             PROF_LAUNCH(PASS_COLS_FUSED,
                         launch_cols_fused_gemm(H, g, tw, twn_log2, ss, p->gemm, status, s));
+        else if (sizeof(R) == 4 && cols_tma_ok(H, g))
+            PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_tma(H, g, 0, tw, twn_log2, &ss, status, s));
         else
             PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g, tw, twn_log2, ss, s));
     } else {
@@ -289,9 +291,13 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         g1.inner_valid = n + 1;
         g1.cols_log2 = cols_log2_for(g1.log2n, celem, maxt);
         const bool gemm = sizeof(R) == 4 && p->gemm >= 0;
+        const bool tma1 = sizeof(R) == 4 && !gemm && cols_tma_ok(H, g1);
         if (gemm)
             PROF_LAUNCH(PASS_COLS_FWD,
                         launch_cols_gemm(H, g1, -1, tw, twn_log2, p->gemm, status, s));
+        else if (tma1)
+            PROF_LAUNCH(PASS_COLS_FWD,
+                        launch_cols_tma(H, g1, -1, tw, twn_log2, nullptr, status, s));
         else
             PROF_LAUNCH(PASS_COLS_FWD, launch_cols<R>(H, g1, -1, tw, twn_log2, s));
         ColGeom g0;
@@ -309,8 +315,16 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
             PROF_LAUNCH(PASS_COLS_INV,
                         launch_cols_gemm(H, g1, +1, tw, twn_log2, p->gemm, status, s));
         } else {
-            PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, ss, s));
-            PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
+            if (sizeof(R) == 4 && cols_tma_ok(H, g0))
+                PROF_LAUNCH(PASS_COLS_FUSED,
+                            launch_cols_tma(H, g0, 0, tw, twn_log2, &ss, status, s));
+            else
+                PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_fused<R>(H, g0, tw, twn_log2, ss, s));
+            if (tma1)
+                PROF_LAUNCH(PASS_COLS_INV,
+                            launch_cols_tma(H, g1, +1, tw, twn_log2, nullptr, status, s));
+            else
+                PROF_LAUNCH(PASS_COLS_INV, launch_cols<R>(H, g1, +1, tw, twn_log2, s));
         }
     }
     // d >= 2 reads S once (R2C) and writes the result once (C2R): Sout may be a

@@ -327,3 +327,39 @@ def test_repeated_T_uses_cached_multipliers_same_result(dims, precision):
     tol = 1e-10 if precision == "fp64" else 2e-4
     assert err_rel(outs[3], oracle.stencil_loop(a0, w, 38, "periodic"), a0) <= tol
     assert err_rel(outs[2], oracle.stencil_loop(a0, w, 37, "periodic"), a0) <= tol
+
+
+# Strided axes of 512..4096 points (the persistent TMA-fed column passes: tiles
+# of 8192 complex values = 8192 / n columns, the last tile ragged) against the
+# loop, element by element; 3-D shapes put the long axis first (fused pass with
+# a mid axis) and second (forward / inverse passes over outer slabs).
+TMA_SHAPES = [((512, 64), "asym", 1), ((1024, 32), "sym", 1), ((2048, 16), "asym", 2),
+              ((4096, 16), "asym", 1), ((4096, 64), "sym", 2), ((512, 16, 8), "asym", 1),
+              ((16, 512, 8), "asym", 1), ((8, 1024, 16), "sym", 2), ((512, 512, 4), "asym", 1)]
+
+
+@pytest.mark.parametrize("dims,kind,r", TMA_SHAPES)
+@pytest.mark.parametrize("T", [1, 3, 50])
+def test_long_strided_axes_match_loop(dims, kind, r, T):
+    w = weights_for(len(dims), kind, r, 40 + r)
+    a0 = wl.grid_uniform(dims, 900 + T)
+    ref = oracle.stencil_loop(a0, w, T, "periodic")
+    got = run_gpu(a0, w, T, "fp32")
+    assert err_rel(got, ref, a0) <= TOL["fp32"]
+
+
+@pytest.mark.parametrize("dims", [(4096, 256), (1024, 64, 32)])
+def test_long_strided_axes_repeated_T_and_large_T(dims):
+    # T = 10^4 against the numpy method (itself pinned to the loop), twice in a
+    # row (the 3-D plan switches to its cached multiplier table on the repeat)
+    w = wl.weights_star(len(dims), 0.6 if len(dims) == 2 else 0.4, 0.1)
+    a0 = wl.grid_with_modes(dims, 77, 3)[0]
+    ref = oracle.stencil_fft_periodic(a0, w, 10000)
+    from paper_2105_06676_gb300 import StencilPlan
+    plan = StencilPlan(dims, w, "periodic", "fp32")
+    for _ in range(2):
+        g = torch.tensor(a0, dtype=torch.float32, device="cuda")
+        plan.run(g, 10000)
+        assert plan.status() == 0
+        assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL["fp32"]
+    plan.close()
