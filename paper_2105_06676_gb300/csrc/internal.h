@@ -83,6 +83,15 @@ bool cols_tma_ok(const void* H, const ColGeom& g);
 cudaError_t launch_cols_tma(void* H, const ColGeom& g, int mode, const void* tw, int twn_log2,
                             const SymbolSet* ps, int* status, cudaStream_t s);
 
+// Persistent bulk-copy-fed passes along the contiguous axis for FP32 grids
+// (rows_tma.cuh), packed row lengths n = 2^8..2^12: dir +1 half spectra ->
+// real rows (src H, dst grid; non-finite output sets bit 0 of *status); dir -1
+// (real rows -> half spectra) is not dispatched. Returns cudaErrorNotSupported when
+// not applicable (the caller then uses the register row kernels).
+bool rows_tma_ok(const void* grid, const void* H, long long Mp, int n_log2, int nrows);
+cudaError_t launch_rows_tma(int dir, const void* src, void* dst, long long Mp, int n_log2,
+                            int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s);
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);
 

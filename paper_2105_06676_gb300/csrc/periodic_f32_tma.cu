@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "cols_tma.cuh"
+#include "rows_tma.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -106,7 +107,54 @@ cudaError_t launch_t(void* H, const ColGeom& g, const CUtensorMap& map, const vo
     return cudaGetLastError();
 }
 
+template <int DIR, int LOG2N>
+cudaError_t launch_rows_t(const void* src, void* dst, long long Mp, int nrows, const void* tw,
+                          int twn_log2, int* status, cudaStream_t s) {
+    const size_t smem = row_tma_smem(LOG2N);
+    auto kern = k_rows_tma<DIR, LOG2N>;
+    cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), smem);
+    if (err != cudaSuccess) return err;
+    const int rpt = row_tma_rows(LOG2N);
+    const long long ntiles = (nrows + rpt - 1) / rpt;
+    const long long slots = 4ll * sm_count();   // four CTAs per SM
+    const int grid = (int)(ntiles < slots ? ntiles : slots);
+    kern<<<grid, kRowThreads, smem, s>>>(static_cast<const float2*>(src), static_cast<float2*>(dst),
+                                         Mp, nrows, static_cast<const float2*>(tw), twn_log2,
+                                         status);
+    return cudaGetLastError();
+}
+
+template <int L, typename F>
+cudaError_t with_row_len(int l, F&& f) {
+    if constexpr (L > kRowTmaLog2Hi) {
+        return cudaErrorNotSupported;
+    } else {
+        if (l == L) return f(std::integral_constant<int, L>{});
+        return with_row_len<L + 1>(l, f);
+    }
+}
+
 }  // namespace
+
+bool rows_tma_ok(const void* grid, const void* H, long long Mp, int n_log2, int nrows) {
+    if (!tma_enabled() || sm_count() <= 0) return false;
+    if (n_log2 < kRowTmaLog2Lo || n_log2 > kRowTmaLog2Hi || nrows < 1) return false;
+    const long long n = 1ll << n_log2;
+    return reinterpret_cast<uintptr_t>(grid) % 16 == 0 && reinterpret_cast<uintptr_t>(H) % 16 == 0 &&
+           Mp % 2 == 0 && Mp >= n + 2;
+}
+
+cudaError_t launch_rows_tma(int dir, const void* src, void* dst, long long Mp, int n_log2,
+                            int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s) {
+    const void* grid = dir < 0 ? src : dst;
+    const void* H = dir < 0 ? dst : src;
+    if (!rows_tma_ok(grid, H, Mp, n_log2, nrows)) return cudaErrorNotSupported;
+    return with_row_len<kRowTmaLog2Lo>(n_log2, [&](auto tag) -> cudaError_t {
+        constexpr int L = decltype(tag)::value;
+        if (dir < 0) return cudaErrorNotSupported;   // R2C: the register row kernel
+        return launch_rows_t<+1, L>(src, dst, Mp, nrows, tw, twn_log2, status, s);
+    });
+}
 
 bool cols_tma_ok(const void* H, const ColGeom& g) {
     if (!tma_enabled() || !encode_tiled() || sm_count() <= 0) return false;
