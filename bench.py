@@ -34,7 +34,7 @@ WORKLOAD = "star5_2d_periodic_4096x4096_T10000"
 # Kernel sources whose hash keys the DRAM traffic recorded under profiles/: a
 # traffic figure is reported only while the kernels are the ones it was taken on.
 KERNEL_SOURCES = ["periodic_kernels.cuh", "fft_ct.cuh", "fft_reg.cuh", "fft_common.cuh",
-                  "symbol.cuh"]
+                  "symbol.cuh", "cols_tma.cuh", "rows_tma.cuh", "periodic_f32_tma.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_star5_2d_4096_fp32.json")
 
 
@@ -307,6 +307,48 @@ def serve_mixed_stream(n_requests: int, seed: int = 5000):
     }
 
 
+def err_rel(got, ref, a0) -> float:
+    """max|got - ref| / max|a_0| (the parity measure of every result)."""
+    import numpy as np
+    return float(np.max(np.abs(np.asarray(got, dtype=np.float64) - ref)) / np.max(np.abs(a0)))
+
+
+def profile_split(plan, grid, pristine, flush, T, launches: int):
+    """Per-kernel CUDA-event split over `launches` solves (a pass of its own, so
+    the timed region above carries no profiling events)."""
+    import torch
+    plan.profile(True)
+    plan.profile_read()
+    for _ in range(launches):
+        grid.copy_(pristine)
+        flush.fill_(2.0)
+        plan.run(grid, T)
+    prof = plan.profile_read()
+    plan.profile(False)
+    torch.cuda.synchronize()
+    return prof
+
+
+def pass_roofline(prof, algo_bytes, peak):
+    """{kind: {us, algorithmic_bytes, GB/s, frac}} for the kinds with a byte count."""
+    out = {}
+    for k, (ms, n) in prof.items():
+        us = 1e3 * ms / n
+        entry = {"us": round(us, 2), "launches": n}
+        if k in algo_bytes:
+            gbs = algo_bytes[k] / (us * 1e-6) / 1e9
+            entry.update({"algorithmic_bytes": algo_bytes[k], "GB_per_s": round(gbs, 1),
+                          "frac": round(gbs / peak, 4)})
+        out[k] = entry
+    return out
+
+
+# GB300 FP64 FMA rate measured once on this pool with a one-kernel
+# microbenchmark (a grid-stride loop of independent DFMA chains on every SM,
+# CUDA events; no clock or power changes).
+FP64_PEAK_TFLOPS_MEASURED = 1.196
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,6 +361,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--no-dirichlet", action="store_true",
                     help="skip the zero-Dirichlet secondary measurement (short profiling runs)")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the FP64 oracle comparisons of the results (short profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -339,10 +383,16 @@ def main():
     from paper_2105_06676_gb300 import StencilPlan
     from paper_2105_06676_gb300 import workloads as wl
 
+    workers = os.cpu_count() or 1
+    check = not args.no_oracle
+    if check:
+        import oracle
+
     wk = wl.star2d_4096("fp32")
     dims, T = wk.dims, wk.T
     N = math.prod(dims)
     a0 = wk.grid()
+    peak, peak_kind = _peaks()
 
     # replicas only: each rank solves its own copy of the workload
     plan32 = StencilPlan(dims, wk.weights, "periodic", "fp32")
@@ -358,71 +408,99 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region: FP32 path, per-kernel events on the launching stream.
-    # One untimed solve first, so that module loading and table setup are not
-    # in the per-kernel averages.
+    # ---- timed region: FP32 path, no profiling events inside it. One untimed
+    # solve first, so that module loading and table setup are outside.
     plan32.run(g32, T)
     plan64.run(g64, T)
     g32.copy_(pristine32)
     g64.copy_(pristine64)
-    torch.cuda.synchronize()
-    plan32.profile(True)
     barrier()
     with ClockSampler(local) as clk:
         times32 = time_solve(plan32, g32, pristine32, flush, args.steps, args.warmup, T)
     barrier()
-    prof = plan32.profile_read()          # warm-up and timed launches
-    plan32.profile(False)
     ms32 = max_over_ranks(sum(times32) / len(times32), world)
     value = job_value(N, T, world, ms32)
     assert plan32.status() == 0
+    out32 = g32.double().cpu().numpy()          # the last timed solve's result
+    # per-kernel split from a separate profiled pass
+    prof = profile_split(plan32, g32, pristine32, flush, T, max(5, args.steps // 2))
 
     # ---- FP64 path (secondary)
     times64 = time_solve(plan64, g64, pristine64, flush, max(3, args.steps // 4), 3, T)
     ms64 = sum(times64) / len(times64)
+    out64 = g64.cpu().numpy()
+    ref2 = oracle.stencil_fft_periodic(a0, wk.weights, T, workers=workers) if check else None
+    err32 = err_rel(out32, ref2, a0) if check else None
+    err64 = err_rel(out64, ref2, a0) if check else None
+    del ref2
 
     # ---- the other periodic configurations (secondary): 1-D heat, FP64;
     # 3-D 7-point star 512^3, FP32 (five passes: R2C, two column FFTs around the
     # fused pass, C2R)
     extra = {}
-    for name, wk_x in (("heat1d_4096_fp64", wl.heat1d_4096()), ("star7_3d_512_fp32", wl.star3d_512("fp32"))):
-        dt = torch.float64 if wk_x.precision == "fp64" else torch.float32
-        plan_x = StencilPlan(wk_x.dims, wk_x.weights, "periodic", wk_x.precision)
-        pris_x = torch.tensor(wk_x.grid(), dtype=dt, device="cuda")
-        g_x = pris_x.clone()
-        times_x = time_solve(plan_x, g_x, pris_x, flush, max(5, args.steps // 2), 3, wk_x.T)
-        assert plan_x.status() == 0
-        ms_x = sorted(times_x)[len(times_x) // 2]
-        extra[name] = {"workload": wk_x.name, "ms_per_step": ms_x,
-                       "value": world * wk_x.n_cells * wk_x.T / (ms_x * 1e-3)}
-        plan_x.close()
-        del g_x, pris_x
+    wk1 = wl.heat1d_4096()
+    plan1 = StencilPlan(wk1.dims, wk1.weights, "periodic", wk1.precision)
+    pris1 = torch.tensor(wk1.grid(), dtype=torch.float64, device="cuda")
+    g1 = pris1.clone()
+    times1 = time_solve(plan1, g1, pris1, flush, max(5, args.steps // 2), 3, wk1.T)
+    assert plan1.status() == 0
+    ms1 = sorted(times1)[len(times1) // 2]
+    extra["heat1d"] = {"workload": wk1.name, "ms_per_step": ms1,
+                       "value": world * wk1.n_cells * wk1.T / (ms1 * 1e-3),
+                       "err_vs_oracle": (err_rel(g1.cpu().numpy(),
+                                                 oracle.stencil_loop(wk1.grid(), wk1.weights, wk1.T),
+                                                 wk1.grid()) if check else None),
+                       "oracle": "FP64 nested loop", "tolerance": 1e-10}
+    plan1.close()
+
+    wk3 = wl.star3d_512("fp32")
+    a3 = wk3.grid()
+    pris3 = torch.tensor(a3, dtype=torch.float32, device="cuda")
+    g3 = pris3.clone()
+    plan3 = StencilPlan(wk3.dims, wk3.weights, "periodic", "fp32")
+    times3 = time_solve(plan3, g3, pris3, flush, max(5, args.steps // 2), 3, wk3.T)
+    assert plan3.status() == 0
+    ms3 = sorted(times3)[len(times3) // 2]
+    out3 = g3.double().cpu().numpy()
+    prof3 = profile_split(plan3, g3, pris3, flush, wk3.T, 5)
+    plan3.close()
+    ref3 = oracle.stencil_fft_periodic(a3, wk3.weights, wk3.T, workers=workers) if check else None
+    H3 = 512 * 512 * 257 * 8
+    G3 = wk3.n_cells * 4
+    algo3 = {"rows_r2c": G3 + H3, "cols_fwd": 2 * H3, "cols_fused": 2 * H3, "cols_inv": 2 * H3,
+             "rows_c2r": H3 + G3}
+    extra["star3d"] = {"workload": wk3.name, "ms_per_step": ms3,
+                       "value": world * wk3.n_cells * wk3.T / (ms3 * 1e-3),
+                       "err_vs_oracle": err_rel(out3, ref3, a3) if check else None,
+                       "oracle": "FP64 StencilFFT-P (numpy/scipy FFT, pinned to the loop)",
+                       "tolerance": 2e-4,
+                       "roofline": {"per_pass": pass_roofline(prof3, algo3, peak),
+                                    "step_bytes": sum(algo3.values()),
+                                    "step_frac": sum(algo3.values()) / (ms3 * 1e-3) / 1e9 / peak,
+                                    "peak": peak, "unit": "GB/s"}}
+    del out3
 
     # ---- tensor-core DFT variants on the 3-D configuration (secondary): the
     # strided-axis radix-16 butterflies as tcgen05 GEMMs; time per solve and the
-    # max difference from the FP32 path relative to max|a_0|
-    wk3 = wl.star3d_512("fp32")
-    pris3 = torch.tensor(wk3.grid(), dtype=torch.float32, device="cuda")
-    g3 = pris3.clone()
-    ref_plan = StencilPlan(wk3.dims, wk3.weights, "periodic", "fp32")
-    ref_plan.run(g3, wk3.T)
-    ref3 = g3.clone()
-    ref_plan.close()
-    amax = float(pris3.abs().max())
+    # error against the FP64 oracle relative to max|a_0|
     gemm_lines = {}
     for prec in ("fp32_gemm_bf16x3", "fp32_gemm_fp16", "fp32_gemm_bf16"):
         plan_g = StencilPlan(wk3.dims, wk3.weights, "periodic", prec)
         times_g = time_solve(plan_g, g3, pris3, flush, max(3, args.steps // 4), 3, wk3.T)
         assert plan_g.status() == 0
         ms_g = sorted(times_g)[len(times_g) // 2]
-        diff = float((g3 - ref3).abs().max()) / amax
         gemm_lines[prec] = {"ms_per_step": ms_g,
                             "value": world * wk3.n_cells * wk3.T / (ms_g * 1e-3),
-                            "max_diff_vs_fp32_rel": diff}
+                            "err_vs_oracle": (err_rel(g3.double().cpu().numpy(), ref3, a3)
+                                              if check else None)}
         plan_g.close()
     del g3, pris3, ref3
 
-    # ---- zero-Dirichlet path (secondary): 8192^2 9-point box, T = 4096, FP32
+    # ---- zero-Dirichlet path (secondary): 8192^2 9-point box, T = 4096, FP32.
+    # Its random weights have no closed-form check at this size; the result is
+    # compared with the FP64 path of the same solve, and a reflection-symmetric
+    # box of the same size, T and schedule is compared with the oracle (method of
+    # images: the periodic solve of the odd extension on 16386^2).
     dirichlet = None
     if not args.no_dirichlet:
         wd = wl.box2d_8192_dirichlet()
@@ -433,10 +511,39 @@ def main():
         times_d = time_solve(pland, gd, pris_d, flush, 2, 1, wd.T)
         ms_d = sum(times_d) / len(times_d)
         assert pland.status() == 0
-        del gd, pris_d
+        outd = gd.double().cpu().numpy()
+        profd = profile_split(pland, gd, pris_d, flush, wd.T, 1)
         pland.close()
+        del gd, pris_d
         dirichlet = {"workload": wd.name, "value": world * wd.n_cells * wd.T / (ms_d * 1e-3),
-                     "ms_per_step": ms_d}
+                     "ms_per_step": ms_d,
+                     "per_kind_ms": {k: round(v[0], 3) for k, v in profd.items()},
+                     "per_kind_launches": {k: v[1] for k, v in profd.items()}}
+        if check:
+            p64 = StencilPlan(wd.dims, wd.weights, "dirichlet", "fp64")
+            gd64 = torch.tensor(ad, dtype=torch.float64, device="cuda")
+            p64.run(gd64, wd.T)
+            assert p64.status() == 0
+            dirichlet["err_vs_fp64_path"] = err_rel(outd, gd64.cpu().numpy(), ad)
+            p64.close()
+            del gd64
+            wsym = np.array([[0.05, 0.1, 0.05], [0.15, 0.3, 0.15], [0.05, 0.1, 0.05]])
+            ps = StencilPlan(wd.dims, wsym, "dirichlet", "fp32")
+            gs = torch.tensor(ad, dtype=torch.float32, device="cuda")
+            ps.run(gs, wd.T)
+            assert ps.status() == 0
+            ext = np.zeros((2 * wd.dims[0] + 2, 2 * wd.dims[1] + 2))
+            ext[1:wd.dims[0] + 1, 1:wd.dims[1] + 1] = ad
+            ext[wd.dims[0] + 2:, 1:wd.dims[1] + 1] = -ad[::-1, :]
+            ext[:, wd.dims[1] + 2:] = -ext[:, wd.dims[1]:0:-1]
+            refs = oracle.stencil_fft_periodic(ext, wsym, wd.T, workers=workers)
+            del ext
+            dirichlet["symmetric_box_err_vs_oracle_images"] = err_rel(
+                gs.double().cpu().numpy(), refs[1:wd.dims[0] + 1, 1:wd.dims[1] + 1], ad)
+            del refs
+            ps.close()
+            del gs
+        del outd
 
     # ---- serving: mixed stream through the continuous-batching server
     serving = serve_mixed_stream(args.serve_requests) if args.serve_requests > 0 else None
@@ -453,9 +560,9 @@ def main():
         plan32.run_host(host_in, T, host_out)
     e2e_s = (time.perf_counter() - t0) / ke
     e2e_value = world * N * T / e2e_s
+    e2e_err = err_rel(host_out.double().numpy(), out32, a0)   # same bits expected as the device run
 
-    # ---- roofline of the dominant kernel (per-launch average over warm-up + timed launches)
-    peak, peak_kind = _peaks()
+    # ---- roofline of the dominant kernel (per-launch average of the profiled pass)
     launches = {k: v[1] for k, v in prof.items()}
     avg_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1]}
     dominant = max(avg_ms, key=lambda k: avg_ms[k])
@@ -466,7 +573,7 @@ def main():
             "rows_c2r": half_bytes + grid_bytes}
     achieved = algo[dominant] / (avg_ms[dominant] * 1e-3) / 1e9
     traffic = kernel_traffic(dominant)
-    step_kernel_launches = sum(launches.values()) / (args.steps + args.warmup)
+    step_kernel_launches = sum(launches.values()) / max(1, args.steps // 2, 5)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -476,6 +583,7 @@ def main():
                          f"of the {T} steps ({dt:.1f} s; work is linear in T)"}
 
     clocks = clk.summary()
+    flops64 = fft2d_flops(dims)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -485,20 +593,25 @@ def main():
             "config": {"workload": WORKLOAD, "grid": list(dims), "T": T, "global_batch": world,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed (512 MiB write) between timed steps; grid restored outside the events"},
+            "err_vs_oracle": err32, "tolerance": 2e-4,
+            "oracle": "FP64 StencilFFT-P (numpy/scipy FFT, pinned to the loop)",
             "fp64_path": {"value": world * N * T / (ms64 * 1e-3), "ms_per_step": ms64,
                           # FP64-ALU bound: 5 n log2 n flops per complex transform
-                          "flops_per_step": fft2d_flops(dims),
-                          "tflops": fft2d_flops(dims) / (ms64 * 1e-3) / 1e12},
+                          "flops_per_step": flops64,
+                          "tflops": flops64 / (ms64 * 1e-3) / 1e12,
+                          "err_vs_oracle": err64, "tolerance": 1e-10},
             "dirichlet_path": dirichlet,
-            "heat1d_path": extra["heat1d_4096_fp64"],
-            "star3d_path": extra["star7_3d_512_fp32"],
-            "star3d_tensor_core_dft": {"workload": wk3.name, **gemm_lines},
+            "heat1d_path": extra["heat1d"],
+            "star3d_path": extra["star3d"],
+            "star3d_tensor_core_dft": {"workload": wk3.name, "tolerance_reported_only": True,
+                                       **gemm_lines},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": grid_bytes,
-                    "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3},
+                    "d2h_bytes_per_step": grid_bytes, "ms_per_step": e2e_s * 1e3,
+                    "err_vs_device_run": e2e_err},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
-                         "per_kernel_ms": {k: round(v, 5) for k, v in avg_ms.items()},
+                         "per_pass": pass_roofline(prof, algo, peak),
                          "algorithmic_bytes": algo[dominant],
                          # the whole solve (three passes) against the same peak
                          "step_bytes": sum(algo.values()),
@@ -508,6 +621,9 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
+        if FP64_PEAK_TFLOPS_MEASURED:
+            line["fp64_path"]["frac_of_measured_fp64_peak"] = (
+                flops64 / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS_MEASURED)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

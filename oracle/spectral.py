@@ -44,12 +44,28 @@ def first_column(weights: np.ndarray, dims) -> np.ndarray:
     return s
 
 
-def symbol_multi_fft(weights: np.ndarray, dims) -> np.ndarray:
+def _fftn(x, workers):
+    """The library Multi-FFT primitive: numpy, or scipy.fft with `workers` threads
+    (same convention: unnormalised forward, 1/N on the inverse)."""
+    if workers is None:
+        return np.fft.fftn(x)
+    import scipy.fft
+    return scipy.fft.fftn(x, workers=workers)
+
+
+def _ifftn(x, workers):
+    if workers is None:
+        return np.fft.ifftn(x)
+    import scipy.fft
+    return scipy.fft.ifftn(x, workers=workers)
+
+
+def symbol_multi_fft(weights: np.ndarray, dims, workers=None) -> np.ndarray:
     """Lambda = Multi-FFT(s): the eigenvalues of S (Step 1, Eq. final_data).
 
     Appendix "Proof of Eigenvalue-FFT Relation": Lambda[k] = (F s)[k].
     """
-    return np.fft.fftn(first_column(weights, dims))
+    return _fftn(first_column(weights, dims), workers)
 
 
 def symbol_closed_form(weights: np.ndarray, dims) -> np.ndarray:
@@ -97,14 +113,20 @@ def symbol_power(lam: np.ndarray, T: int) -> np.ndarray:
     return V
 
 
-def stencil_fft_periodic(a0: np.ndarray, weights: np.ndarray, T: int) -> np.ndarray:
-    """StencilFFT-P (Fig. "stencil-fft-algorithm-dD"): a_T = F^-1 Lambda^T F a_0."""
+def stencil_fft_periodic(a0: np.ndarray, weights: np.ndarray, T: int,
+                         workers=None) -> np.ndarray:
+    """StencilFFT-P (Fig. "stencil-fft-algorithm-dD"): a_T = F^-1 Lambda^T F a_0.
+
+    `workers` selects scipy.fft with that many threads as the Multi-FFT
+    primitive (large grids); the steps are the same."""
     a0 = np.asarray(a0, dtype=np.float64)
-    lam = symbol_multi_fft(weights, a0.shape)        # Step 1 (i)
-    x = np.fft.fftn(a0)                               # Step 1 (ii)
-    V = symbol_power(lam, T)                          # Step 2
-    y = V * x                                         # Step 3
-    return np.fft.ifftn(y).real                       # Step 4 (real grid)
+    lam = symbol_multi_fft(weights, a0.shape, workers)   # Step 1 (i)
+    x = _fftn(a0, workers)                               # Step 1 (ii)
+    V = symbol_power(lam, T)                             # Step 2
+    del lam
+    y = V * x                                            # Step 3
+    del V, x
+    return _ifftn(y, workers).real                       # Step 4 (real grid)
 
 
 def dft_naive(x: np.ndarray) -> np.ndarray:

@@ -77,13 +77,41 @@ def test_dirichlet_method_of_images_full_size_2d():
     dims, T = (1024, 1024), 500
     w = np.array([[0.05, 0.1, 0.05], [0.15, 0.3, 0.15], [0.05, 0.1, 0.05]])
     a0 = wl.grid_uniform(dims, 17)
-    ext = np.zeros((2 * dims[0] + 2, 2 * dims[1] + 2))
-    ext[1:dims[0] + 1, 1:dims[1] + 1] = a0
-    ext[dims[0] + 2:, 1:dims[1] + 1] = -a0[::-1, :]
-    ext[:, dims[1] + 2:] = -ext[:, dims[1]:0:-1]
-    ref = oracle.stencil_fft_periodic(ext, w, T)[1:dims[0] + 1, 1:dims[1] + 1]
+    ref = oracle.stencil_fft_periodic(odd_extension_2d(a0), w, T)[1:dims[0] + 1, 1:dims[1] + 1]
     for prec in ("fp64", "fp32"):
         assert err_rel(run_gpu(a0, w, T, prec), ref, a0) <= TOL[prec]
+
+
+def odd_extension_2d(a0):
+    """Odd extension in both axes: 2 (l + 1) cells per axis, a_0 in [1, l]."""
+    l0, l1 = a0.shape
+    ext = np.zeros((2 * l0 + 2, 2 * l1 + 2))
+    ext[1:l0 + 1, 1:l1 + 1] = a0
+    ext[l0 + 2:, 1:l1 + 1] = -a0[::-1, :]
+    ext[:, l1 + 2:] = -ext[:, l1:0:-1]
+    return ext
+
+
+def test_box9_8192_full_size_method_of_images():
+    # the benchmark's size, T and schedule (sigma T = l/2: empty interior, the
+    # full recursion and its graph) with a reflection-symmetric 9-point box, so
+    # that zero Dirichlet on 8192^2 equals the periodic solve of the odd
+    # extension on 16386^2, compared element by element
+    import os
+    wk = wl.box2d_8192_dirichlet()
+    w = np.array([[0.05, 0.1, 0.05], [0.15, 0.3, 0.15], [0.05, 0.1, 0.05]])
+    a0 = wk.grid()
+    ref = oracle.stencil_fft_periodic(odd_extension_2d(a0), w, wk.T,
+                                      workers=os.cpu_count())[1:8193, 1:8193]
+    from paper_2105_06676_gb300 import StencilPlan
+    plan = StencilPlan(a0.shape, w, "dirichlet", "fp32")
+    g0 = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    for _ in range(2):          # eager first run, then the captured graph
+        g = g0.clone()
+        plan.run(g, wk.T)
+        assert plan.status() == 0
+        assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4
+    plan.close()
 
 
 @pytest.mark.parametrize("T", [64, 100])

@@ -312,6 +312,20 @@ def test_method_of_images_2d():
         assert rel_err(stencil_loop(a0, w, T, "dirichlet"), per) < 1e-12
 
 
+def test_method_of_images_2d_threaded_fft_primitive():
+    # the same pin through scipy.fft with threads as the Multi-FFT primitive
+    # (used for the full-size odd extensions, 2 (l + 1) = 2 * 3 * 2731 points)
+    w = np.array([[0.05, 0.1, 0.05], [0.15, 0.3, 0.15], [0.05, 0.1, 0.05]])
+    a0 = wl.grid_uniform((13, 9), 14)
+    ext, n0 = _odd_extend(a0, 0)
+    ext, n1 = _odd_extend(ext, 1)
+    for T in (3, 40):
+        per = stencil_fft_periodic(ext, w, T, workers=2)[1:n0 + 1, 1:n1 + 1]
+        assert rel_err(stencil_loop(a0, w, T, "dirichlet"), per) < 1e-12
+        np.testing.assert_allclose(per, stencil_fft_periodic(ext, w, T)[1:n0 + 1, 1:n1 + 1],
+                                   rtol=0, atol=1e-13)
+
+
 # --------------------------------------------------------------------------
 # 7. spectral pieces: symbol, DFT convention, repeated squaring
 # --------------------------------------------------------------------------
