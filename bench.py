@@ -363,6 +363,9 @@ def main():
                     help="skip the zero-Dirichlet secondary measurement (short profiling runs)")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the FP64 oracle comparisons of the results (short profiling runs)")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline solve only: no secondary configurations, serving or "
+                         "end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -424,6 +427,16 @@ def main():
     out32 = g32.double().cpu().numpy()          # the last timed solve's result
     # per-kernel split from a separate profiled pass
     prof = profile_split(plan32, g32, pristine32, flush, T, max(5, args.steps // 2))
+
+    if args.only_headline:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+                "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
 
     # ---- FP64 path (secondary)
     times64 = time_solve(plan64, g64, pristine64, flush, max(3, args.steps // 4), 3, T)
