@@ -104,9 +104,31 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
  *   grid    device pointer to prod(dims) elements (double for FP64 plans,
  *           float for FP32 plans), 16-byte aligned.
  *   stream  a cudaStream_t (NULL = legacy default stream).
- * Enqueues work only; returns before the GPU finishes. T == 0 is a no-op.
+ * Periodic plans: enqueues work only and allocates nothing; returns before the
+ * GPU finishes. Zero-Dirichlet plans: the same once T has been prepared (by
+ * stencil_prepare or an earlier run with this T); a first run for a T that
+ * was not prepared builds the RecursiveBoundary schedule, which allocates
+ * device memory (cudaMalloc, an implicit device synchronisation) and waits for
+ * the upload of its tables on the calling thread's per-thread stream. The
+ * second run for a (T, grid) pair captures a CUDA graph (host work only) that
+ * later runs replay. T == 0 is a no-op.
  */
 int stencil_run(stencil_plan_t plan, void* grid, int64_t T, void* stream);
+
+/*
+ * Do the per-T set-up of stencil_run ahead of time, so that runs with this T
+ * allocate nothing and do not synchronise (paper Sec. 4 "Step 2": the symbol
+ * power depends on T only; Sec. 5: the RecursiveBoundary schedule depends on
+ * T and the grid shape only).
+ *   Zero-Dirichlet plans: builds the schedule, its buffers and its uploaded
+ *   tables (allocates; waits for the uploads on the per-thread stream).
+ *   Periodic plans that keep a multiplier table (3-D, and 1-D axes of 32 ..
+ *   2^15 points FP32 / 2^14 FP64): builds Lambda^T / N for T on `stream`, so
+ *   the next run with T uses it; other periodic plans: nothing to do.
+ * T == 0 is a no-op. Returns STENCIL_OK, STENCIL_EINVAL (null plan, T < 0),
+ * STENCIL_ENOMEM or STENCIL_ECUDA.
+ */
+int stencil_prepare(stencil_plan_t plan, int64_t T, void* stream);
 
 /*
  * End-to-end variant of stencil_run on host memory; synchronises the stream
@@ -243,11 +265,12 @@ int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_
  * stencil_noalloc_scratch_bytes() bytes (32 MiB) that every GPU loading this
  * library holds until exit. Sizes whose scratch does not fit return
  * STENCIL_EUNSUPPORTED (e.g. a 2-D FP32 grid holds up to 2048 x 2048 cells);
- * bad arguments return STENCIL_EINVAL. The first call on a device sets that
- * device up (looks up the array's address) and should come before any stream
- * capture. Calls share the array: calls whose work overlaps on the GPU race and
- * must be serialised by the caller. Non-finite output is not reported. Calls no
- * allocating routine.
+ * bad arguments return STENCIL_EINVAL. Every call looks up the array's address
+ * on the current device (after a device reset the array is found again); the
+ * first call on a device loads the library's module there and should come
+ * before any stream capture. Calls share the array: calls whose work overlaps
+ * on the GPU race and must be serialised by the caller. Non-finite output is
+ * not reported. Calls no allocating routine.
  */
 int stencil_periodic_run_noalloc(int ndim, const int64_t* dims, int radius,
                                  const double* weights, int precision, void* grid,
@@ -319,7 +342,9 @@ const char* stencil_strerror(int code);
  */
 int64_t stencil_max_axis(int ndim, int precision, int axis);
 
-/* Bytes of device workspace a plan with these arguments allocates (0 on error). */
+/* Bytes of device workspace a plan with these arguments allocates: the half
+ * spectrum, plus for periodic plans that keep one the Lambda^T / N table (0 on
+ * error). */
 size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int boundary,
                                int precision);
 

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("stencil_run", _c.c_int, [_vp, _vp, _c.c_int64, _vp]),
     ("stencil_run_host", _c.c_int, [_vp, _vp, _vp, _c.c_int64, _vp]),
     ("stencil_symbol_power", _c.c_int, [_vp, _c.c_int64, _vp, _vp]),
+    ("stencil_prepare", _c.c_int, [_vp, _c.c_int64, _vp]),
     ("stencil_status", _c.c_int, [_vp, _vp]),
     ("stencil_destroy", _c.c_int, [_vp]),
     ("stencil_strerror", _c.c_char_p, [_c.c_int]),

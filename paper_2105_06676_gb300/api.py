@@ -89,6 +89,12 @@ class StencilPlan:
         _capi.check(_capi.lib().stencil_plan_set_schedule(self._handle, code),
                     "stencil_plan_set_schedule")
 
+    def prepare(self, T: int, stream=None) -> None:
+        """Per-T set-up ahead of the first run (stencil_prepare): afterwards runs
+        with this T allocate nothing and do not synchronise."""
+        _capi.check(_capi.lib().stencil_prepare(self._handle, int(T), _stream_ptr(stream)),
+                    "stencil_prepare")
+
     def run(self, grid, T: int, stream=None):
         """Advance a CUDA tensor of shape dims in place by T steps (async); returns it."""
         if not grid.is_cuda or grid.dtype != self.dtype or tuple(grid.shape) != self.dims \

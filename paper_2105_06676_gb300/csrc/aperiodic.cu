@@ -1798,18 +1798,13 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
     return cudaSuccess;
 }
 
-template <typename R>
-static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStream_t s) {
-    const int sigma = p->radius;
-    if (sigma == 0)  // a pointwise stencil never feels the boundary
-        return periodic_solve<R>(p, grid, p->dims, T, p->H, p->Mp, p->tw, p->twn_log2, p->E64,
-                                 p->E32, p->status, s);
+// The schedule of T with every buffer it needs, including the interior scratch.
+static cudaError_t prepare_all(stencil_plan_s* p, int64_t T, Schedule** out) {
+    cudaError_t err = prepare(p, T, out);
+    if (err != cudaSuccess) return err;
     int64_t maxdist = p->dims[0] / 2;
     for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
-    Schedule* sc = nullptr;
-    cudaError_t err = prepare(p, T, &sc);
-    if (err != cudaSuccess) return err;
-    const bool interior = !sc->loop && sigma * T < maxdist;
+    const bool interior = !(*out)->loop && p->radius * T < maxdist;
     AperiodicState* st = p->ap;
     if (interior && !st->Z) {
         err = cudaMalloc(&st->Z, (size_t)p->n_cells * p->elem);
@@ -1819,6 +1814,22 @@ static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStr
         }
         st->bytes += (size_t)p->n_cells * p->elem;
     }
+    return cudaSuccess;
+}
+
+template <typename R>
+static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStream_t s) {
+    const int sigma = p->radius;
+    if (sigma == 0)  // a pointwise stencil never feels the boundary
+        return periodic_solve<R>(p, grid, p->dims, T, p->H, p->Mp, p->tw, p->twn_log2, p->E64,
+                                 p->E32, p->status, s);
+    int64_t maxdist = p->dims[0] / 2;
+    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
+    Schedule* sc = nullptr;
+    cudaError_t err = prepare_all(p, T, &sc);
+    if (err != cudaSuccess) return err;
+    const bool interior = !sc->loop && sigma * T < maxdist;
+    AperiodicState* st = p->ap;
     // profiled runs: one stream, every launch bracketed by events
     if (p->prof.enabled) return emit<R>(p, st, *sc, grid, T, interior, s, false);
     // the first run for a T goes eagerly (it also sets every kernel attribute)
@@ -1941,6 +1952,16 @@ int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s) {
     cudaError_t err = p->precision == STENCIL_FP32
                           ? aperiodic_impl<float>(p, static_cast<float*>(grid), T, s)
                           : aperiodic_impl<double>(p, static_cast<double*>(grid), T, s);
+    if (err == cudaSuccess) return STENCIL_OK;
+    if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
+    if (err == cudaErrorInvalidValue) return STENCIL_EUNSUPPORTED;
+    return STENCIL_ECUDA;
+}
+
+int aperiodic_prepare(stencil_plan_s* p, int64_t T) {
+    if (p->radius == 0) return STENCIL_OK;   // solved by the periodic path
+    Schedule* sc = nullptr;
+    const cudaError_t err = prepare_all(p, T, &sc);
     if (err == cudaSuccess) return STENCIL_OK;
     if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
     if (err == cudaErrorInvalidValue) return STENCIL_EUNSUPPORTED;

@@ -22,13 +22,13 @@
 //     tile's load, which lands while this CTA finishes its last butterflies and
 //     stores and while the SM's other CTA computes;
 //   * results go straight from registers to global memory.
-// A wait that gives up after kSpinLimit polls records kGemmTimeout (bit 2 of
+// A wait that gives up after kWaitLimitNs records kGemmTimeout (bit 2 of
 // the status word) and ends the CTA (no load is then in flight).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "dft_gemm.cuh"   // smem_u32, mbar_init, mbar_wait, fence_async_shared, kSpinLimit
+#include "dft_gemm.cuh"   // smem_u32, mbar_init, mbar_wait (time-bounded), fence_async_shared
 #include "fft_ct.cuh"
 #include "internal.h"
 #include "symbol.cuh"

@@ -21,9 +21,12 @@
 // Synchronisation per stage: every thread writes its A row, makes it visible
 // to the tensor core's async proxy (fence.proxy.async) and meets the others at
 // a barrier; thread 0 issues the MMAs and commits them to an mbarrier; all
-// threads wait on it (bounded: after kSpinLimit polls the kernel records
-// kGemmTimeout in its status word, waits once more with the same bound and
-// carries on with whatever is in tensor memory), then load their row.
+// threads wait on it, then load their row. Waits are bounded in time
+// (kWaitLimitNs of %globaltimer): a CTA whose wait runs out records kGemmTimeout
+// in its status word and sets its abandoned flag; from then on it issues no
+// MMA and waits on nothing (its remaining butterflies return whatever tensor
+// memory holds, and the status word reports the failure), and before releasing
+// tensor memory it waits once more (bounded) for the abandoned stage's MMAs.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -40,7 +43,7 @@ constexpr int kGemmBF16x3 = 2;
 
 constexpr int kGemmRows = 256;            // butterflies (threads) per CTA
 constexpr int kGemmTmemCols = 64;         // two 128-row tiles x 32 FP32 columns
-constexpr unsigned kSpinLimit = 1u << 22; // mbarrier polls before giving up
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per bounded wait
 constexpr int kGemmTimeout = 4;           // status bit for an abandoned wait
 
 // Shared-memory operand layout, K-major without swizzle: 8-row x 16-byte core
@@ -105,9 +108,17 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 
-// Bounded wait for the mbarrier phase with parity `parity`; false on timeout.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase with parity `parity`, bounded in time
+// (kWaitLimitNs of the global nanosecond timer); false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (unsigned i = 0; i < kSpinLimit; ++i) {
+    unsigned long long start = 0;
+    for (unsigned i = 0;; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -117,8 +128,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (i == 0) start = global_ns();
+        else if ((i & 63) == 0 && global_ns() - start > kWaitLimitNs) return false;
+        if (i == 0xFFFFFFFFu) return false;   // backstop should the timer not advance
     }
-    return false;
 }
 
 // 32 consecutive FP32 columns of this thread's tensor-memory lane.
@@ -165,20 +178,28 @@ struct DftGemm {
     uint32_t tmem;           // tensor-memory base (lane 0, column 0)
     uint32_t phase;          // parity of the next mbarrier phase
     int* status;
+    // shared words: [0] abandoned (a wait ran out), [1] an MMA commit of the
+    // abandoned stage was issued, [2] that stage's phase
+    uint32_t* flags;
+    // test hook: issue no MMA and no commit, so that every wait runs out
+    bool skip_commit;
 
     static constexpr size_t smem_bytes() {
-        return (size_t)kTerms * kABytes + 2 * (size_t)kTerms * kBBytes + 16;
+        return (size_t)kTerms * kABytes + 2 * (size_t)kTerms * kBBytes + 32;
     }
 
     // Builds B (both directions), initialises the mbarrier and allocates
     // tensor memory. Every thread of the CTA calls it; it ends with a barrier.
-    __device__ void init(unsigned char* smem, uint32_t* tmem_slot, int* st) {
+    __device__ void init(unsigned char* smem, uint32_t* tmem_slot, int* st, bool no_commit) {
         a = smem;
         b = smem + kTerms * kABytes;
         unsigned char* mb = b + 2 * kTerms * kBBytes;
         mbar = smem_u32(mb);
+        flags = reinterpret_cast<uint32_t*>(mb + 16);
         status = st;
         phase = 0;
+        skip_commit = no_commit;
+        if (threadIdx.x < 3) flags[threadIdx.x] = 0;
         // B[n][k] for n < 16: Re y_n from (Re x_k | Im x_k); n >= 16: Im y_(n-16)
         for (int e = threadIdx.x; e < 2 * 32 * 32; e += blockDim.x) {
             const int dir = e >> 10;             // 0: forward (w = e^{-2 pi i/16}), 1: inverse
@@ -214,11 +235,14 @@ struct DftGemm {
         tmem = *tmem_slot;
     }
 
-    // Releases tensor memory. Every thread calls it after its last dft16.
+    // Releases tensor memory. Every thread calls it after its last dft16. After
+    // an abandoned wait whose MMAs were issued, first waits once more (bounded)
+    // for them.
     __device__ void finish() {
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        if (flags[0] && flags[1]) mbar_wait(mbar, flags[2]);
         if (threadIdx.x < 32)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                          "r"((uint32_t)kGemmTmemCols)
@@ -270,7 +294,8 @@ struct DftGemm {
         fence_async_shared();
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        const bool abandoned = flags[0] != 0;   // set before the barrier above
+        if (threadIdx.x == 0 && !abandoned && !skip_commit) {
             tc_fence_after();
             constexpr uint32_t idesc = gemm_idesc(MODE == kGemmFP16 ? 0 : 1);
             const unsigned char* bd = b + (size_t)(DIR < 0 ? 0 : 1) * kTerms * kBBytes;
@@ -294,13 +319,16 @@ struct DftGemm {
             }
             mma_commit(mbar);
         }
-        bool ok = mbar_wait(mbar, phase);
-        if (!ok) {
-            // record the abandoned wait, then wait once more (also bounded) so
-            // that no MMA of this stage is still running when the accumulators
-            // are read or the tensor memory is released
-            if (threadIdx.x % 32 == 0) atomicOr(status, kGemmTimeout);
-            ok = mbar_wait(mbar, phase);
+        const bool ok = abandoned || mbar_wait(mbar, phase);
+        if (__syncthreads_or(!ok) && !abandoned) {
+            // the first abandoned wait of this CTA: record it; later stages issue
+            // nothing and wait on nothing (flags are read after the next barrier)
+            if (threadIdx.x == 0) {
+                atomicOr(status, kGemmTimeout);
+                flags[0] = 1;
+                flags[1] = skip_commit ? 0u : 1u;
+                flags[2] = phase;
+            }
         }
         phase ^= 1;
         tc_fence_after();

@@ -12,9 +12,11 @@
 // process exits. The caller still passes the grid.
 //
 // Host code may not use g_noalloc_scratch's name as a device address: on the
-// host it is only a stand-in. The first call on each device, with that device
-// current, looks the address up with cudaGetSymbolAddress and caches it; that
-// first call should therefore come before any stream capture on the device.
+// host it is only a stand-in. Every call looks the array's address up with
+// cudaGetSymbolAddress on the current device (so a device reset, after which
+// the module and the array are loaded again, never leaves a stale address).
+// The first call on a device loads the module there and should therefore come
+// before any stream capture on that device.
 // Every call shares the one array and leaves its contents behind: calls whose
 // work overlaps on the GPU (on different streams, or from different host
 // threads) race on it and must be serialised by the caller.
@@ -22,7 +24,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/stencilfft.h"
 #include "internal.h"
@@ -33,28 +34,15 @@ using namespace sfft;
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device (set up once per
-// device).
+// Device address of g_noalloc_scratch on the current device.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (err != cudaSuccess) return err;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return err;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

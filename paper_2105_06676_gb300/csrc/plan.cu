@@ -190,6 +190,20 @@ static cudaError_t alloc_tables(stencil_plan_s* p) {
     return err;
 }
 
+// Bytes of the Lambda^T / N table a periodic plan keeps for a repeated T: 3-D
+// plans (one half spectrum) and 1-D axes one CTA holds (n + 1 values); 0 for the
+// other shapes, which evaluate the multiplier inside their fused pass.
+size_t multiplier_table_bytes(int ndim, const int64_t* dims, int precision) {
+    const size_t celem = precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
+    if (ndim == 3) return periodic_workspace_bytes(ndim, dims, precision);
+    if (ndim == 1) {
+        const int64_t n = dims[0] / 2;
+        const int64_t cap = 16 * (precision == STENCIL_FP32 ? kMaxThreadsF32 : kMaxThreadsF64);
+        if (n >= 16 && n <= cap) return (size_t)(n + 1) * celem;
+    }
+    return 0;
+}
+
 size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision) {
     if (ndim == 1) return 0;
     const size_t celem = precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
@@ -438,7 +452,10 @@ static int validate(int ndim, const int64_t* dims, int radius, int boundary, int
 size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int boundary,
                                int precision) {
     if (validate(ndim, dims, radius, boundary, precision) != STENCIL_OK) return 0;
-    return periodic_workspace_bytes(ndim, dims, base_precision(precision));
+    const int bp = base_precision(precision);
+    size_t bytes = periodic_workspace_bytes(ndim, dims, bp);
+    if (boundary == STENCIL_PERIODIC) bytes += multiplier_table_bytes(ndim, dims, bp);
+    return bytes;
 }
 
 int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
@@ -484,6 +501,19 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
             p->dev_bytes += p->H_bytes;
         }
     }
+    // storage for the repeated-T multiplier table (built by a run that repeats
+    // the previous T, or by stencil_prepare); without room the passes evaluate
+    if (err == cudaSuccess && boundary == STENCIL_PERIODIC) {
+        const size_t vbytes = multiplier_table_bytes(ndim, dims, precision);
+        if (vbytes) {
+            if (cudaMalloc(&p->vt, vbytes) == cudaSuccess) {
+                p->dev_bytes += vbytes;
+            } else {
+                p->vt = nullptr;
+                cudaGetLastError();
+            }
+        }
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(cudaStreamPerThread);
     if (err != cudaSuccess) {
         free_plan(p);
@@ -519,42 +549,33 @@ int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
 // The multiplier table of a periodic 3-D or one-CTA 1-D plan (paper Sec. 4
 // "Step 2": the symbol power is computed once per T and reused): a run
 // evaluates Lambda^T inside its fused pass, unless the previous run had the
-// same T -- then the table is built across the whole GPU (FP64 powers,
-// stored at pass precision) and kept for T. Measured on GB300: the 3-D fused
-// pass gains (512^3 solve 1.75 -> 1.32 ms; its per-column symbol set-up is
-// the costly part), and so does a 1-D axis solved by one CTA, which otherwise
+// same T (or stencil_prepare asked for it) -- then the table is built across
+// the whole GPU (FP64 powers, stored at pass precision) into storage the plan
+// allocated at creation, and kept for T. Measured on GB300: the 3-D fused pass
+// gains (512^3 solve 1.75 -> 1.32 ms; its per-column symbol set-up is the
+// costly part), and so does a 1-D axis solved by one CTA, which otherwise
 // evaluates every FP64 power itself; the 2-D pass loses (the table's extra
 // read outweighs the arithmetic it saves), so 2-D evaluates.
+static cudaError_t build_table(stencil_plan_s* p, int64_t T, cudaStream_t s) {
+    const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
+    cudaError_t err = p->precision == STENCIL_FP32 ? launch_vtable<float>(p->vt, sp, p->Mp, s)
+                                                   : launch_vtable<double>(p->vt, sp, p->Mp, s);
+    if (err == cudaSuccess) p->vt_T = T;
+    return err;
+}
+
 static cudaError_t periodic_table(stencil_plan_s* p, int64_t T, cudaStream_t s, const void** out) {
     *out = nullptr;
-    // 1-D axes one CTA holds (their single CTA would otherwise evaluate every
-    // FP64 power itself) and 3-D
-    const bool one_cta_1d = p->ndim == 1 && p->dims[0] / 2 >= 16 &&
-                            p->dims[0] / 2 <= 16 * (p->precision == STENCIL_FP32 ? kMaxThreadsF32
-                                                                                : kMaxThreadsF64);
-    if (p->ndim != 3 && !one_cta_1d) return cudaSuccess;
-    if (p->vt && p->vt_T == T) {
+    if (!p->vt) return cudaSuccess;   // shape without a table, or no room for it
+    if (p->vt_T == T) {
         *out = p->vt;
         return cudaSuccess;
     }
     const bool repeat = p->last_T == T;
     p->last_T = T;
     if (!repeat) return cudaSuccess;
-    const size_t vbytes = p->ndim == 1 ? (size_t)(p->dims[0] / 2 + 1) * 2 * p->elem : p->H_bytes;
-    if (!p->vt) {
-        cudaError_t err = cudaMalloc(&p->vt, vbytes);
-        if (err != cudaSuccess) {
-            p->vt = nullptr;
-            cudaGetLastError();
-            return cudaSuccess;   // no room for the table: keep evaluating in the pass
-        }
-        p->dev_bytes += vbytes;
-    }
-    const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
-    cudaError_t err = p->precision == STENCIL_FP32 ? launch_vtable<float>(p->vt, sp, p->Mp, s)
-                                                   : launch_vtable<double>(p->vt, sp, p->Mp, s);
+    cudaError_t err = build_table(p, T, s);
     if (err != cudaSuccess) return err;
-    p->vt_T = T;
     *out = p->vt;
     return cudaSuccess;
 }
@@ -615,6 +636,16 @@ int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int6
     return from_cuda(cudaStreamSynchronize(s));
 }
 
+int stencil_prepare(stencil_plan_t p, int64_t T, void* stream) {
+    if (!p || T < 0) return STENCIL_EINVAL;
+    if (T == 0) return STENCIL_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->boundary == STENCIL_ZERO_DIRICHLET) return aperiodic_prepare(p, T);
+    if (!p->vt || p->vt_T == T) return STENCIL_OK;
+    p->last_T = T;
+    return from_cuda(build_table(p, T, s));
+}
+
 int stencil_symbol_power(stencil_plan_t p, int64_t T, void* out, void* stream) {
     if (!p || !out || T < 0) return STENCIL_EINVAL;
     const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
@@ -649,6 +680,16 @@ int stencil_destroy(stencil_plan_t p) {
     free_plan(p);
     return STENCIL_OK;
 }
+
+}  // extern "C"
+
+namespace sfft {
+// Frees a plan that has no work in flight (its last use has completed), without
+// waiting for the rest of the device.
+void plan_free_idle(stencil_plan_s* p) { free_plan(p); }
+}  // namespace sfft
+
+extern "C" {
 
 }  // extern "C"
 

@@ -88,6 +88,9 @@ struct stencil_plan_s {
 };
 
 namespace sfft {
+// Frees a plan none of whose work is still in flight, without a device-wide
+// synchronisation (stencil_destroy waits for the whole device).
+void plan_free_idle(stencil_plan_s* p);
 int ilog2_exact(int64_t v);
 void plan_set_weights(stencil_plan_s* p, int radius, const double* w);
 int64_t max_axis(int ndim, int precision, int axis);
@@ -95,6 +98,7 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
                                 const double2* const* E64, const float2* const* E32,
                                 const int* perm);
 size_t periodic_workspace_bytes(int ndim, const int64_t* dims, int precision);
+size_t multiplier_table_bytes(int ndim, const int64_t* dims, int precision);
 template <typename R>
 cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items, int64_t T,
                           void* H, long long Mp, const int* orient, const int (*perms)[3],
@@ -110,6 +114,9 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
 }  // namespace sfft
 
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
+// Builds the schedule, buffers and uploaded tables of T ahead of the first run
+// (allocates; waits for the uploads); returns a status code.
+int aperiodic_prepare(stencil_plan_s* p, int64_t T);
 // Measures the schedule candidates for T and keeps the fastest; returns its
 // index (times in ms[i] for i < cap) or a negative status.
 int aperiodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStream_t s,

@@ -22,7 +22,7 @@
 //     while the SM's other CTAs compute.
 // R2C writes the half spectrum X[0..n] of each row (row stride Mp); C2R reads
 // Y[0..n+1] of each row (one padding element beyond Y[n], inside the row
-// stride) and writes the real row. A wait that gives up after kSpinLimit polls
+// stride) and writes the real row. A wait that gives up after kWaitLimitNs
 // records kGemmTimeout (bit 2 of the status word) and ends the CTA.
 #include <cuda_runtime.h>
 #include <stdint.h>

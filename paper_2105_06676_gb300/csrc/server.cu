@@ -18,6 +18,12 @@
 //
 // Latency is measured from submit to the worker observing the request's
 // completion event.
+//
+// Locking: the mutex guards the queue, the results and the statistics. The
+// plan pool and the slots belong to the worker thread alone, so plan creation
+// and eviction run with the mutex released: a submit never waits for them. An
+// evicted plan is idle -- the completion event of its last launch has been
+// observed -- and is freed without a device-wide synchronisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,6 +80,7 @@ struct PlanEntry {
     void* stackH = nullptr;
     void* vt[kMaxItems] = {};
     size_t cells = 0, h_item = 0, v_item = 0;
+    cudaEvent_t last = nullptr;   // recorded after the plan's latest launch
 };
 
 struct Slot {
@@ -83,6 +90,7 @@ struct Slot {
     std::vector<Pending> reqs;
     PlanEntry* pe = nullptr;
     int status = STENCIL_OK;
+    int batched = 0;   // requests of the last launch, when it was a batch
 };
 
 int validate_request(const stencil_request* r) {
@@ -172,8 +180,14 @@ struct stencil_server_s {
     void complete(Slot& sl, double t);
 };
 
+// Frees an idle plan: its last launch has completed (the event is waited on,
+// which returns at once for an idle plan), so no device-wide synchronisation.
 void stencil_server_s::release_plan(PlanEntry* pe) {
-    if (pe->plan) stencil_destroy(pe->plan);
+    if (pe->last) {
+        cudaEventSynchronize(pe->last);
+        cudaEventDestroy(pe->last);
+    }
+    if (pe->plan) plan_free_idle(pe->plan);
     cudaFree(pe->stackS);
     cudaFree(pe->stackH);
     for (void* v : pe->vt) cudaFree(v);
@@ -224,6 +238,8 @@ PlanEntry* stencil_server_s::acquire(const Key& k, int* status) {
         for (int i = 0; i < kMaxItems && err == cudaSuccess; ++i) err = cudaMalloc(&pe->vt[i], pe->v_item);
         if (err != cudaSuccess) rc = err == cudaErrorMemoryAllocation ? STENCIL_ENOMEM : STENCIL_ECUDA;
     }
+    if (rc == STENCIL_OK && cudaEventCreateWithFlags(&pe->last, cudaEventDisableTiming) != cudaSuccess)
+        rc = STENCIL_ECUDA;
     if (rc != STENCIL_OK) {
         *status = rc;
         release_plan(pe);
@@ -285,8 +301,7 @@ int stencil_server_s::launch(Slot& sl) {
                               static_cast<char*>(pe->stackS) + i * pe->cells * elem,
                               pe->cells * elem, cudaMemcpyDeviceToDevice, sl.stream);
     if (err != cudaSuccess) return err == cudaErrorMemoryAllocation ? STENCIL_ENOMEM : STENCIL_ECUDA;
-    ++stats.batched_launches;
-    stats.batched_requests += items;
+    sl.batched = items;   // counted in the statistics under the lock
     return STENCIL_OK;
 }
 
@@ -334,11 +349,15 @@ bool stencil_server_s::admit_one(std::unique_lock<std::mutex>& lock) {
             break;
         }
     if (!sl) return false;
-    const stencil_request& head = pending.front().r;
+    const stencil_request head = pending.front().r;
     const bool batch = batchable(head);
     const Key k = key_of(head, batch);
     int status = STENCIL_OK;
+    // plan pool work (eviction, creation) without the lock; the head stays at
+    // the front meanwhile (only this thread removes requests)
+    lock.unlock();
     PlanEntry* pe = acquire(k, &status);
+    lock.lock();
     if (!pe) {
         if (status == STENCIL_OK) return false;   // wait for memory to free up
         Pending q = pending.front();
@@ -369,13 +388,20 @@ bool stencil_server_s::admit_one(std::unique_lock<std::mutex>& lock) {
     sl->pe = pe;
     sl->busy = true;
     lock.unlock();
+    sl->batched = 0;
     sl->status = launch(*sl);
     if (sl->status == STENCIL_OK) {
-        if (cudaEventRecord(sl->done, sl->stream) != cudaSuccess) sl->status = STENCIL_ECUDA;
+        if (cudaEventRecord(sl->done, sl->stream) != cudaSuccess ||
+            cudaEventRecord(pe->last, sl->stream) != cudaSuccess)
+            sl->status = STENCIL_ECUDA;
     }
     int busy = 0;
     for (Slot& s : slots) busy += s.busy;
     lock.lock();
+    if (sl->batched) {
+        ++stats.batched_launches;
+        stats.batched_requests += sl->batched;
+    }
     stats.max_in_flight = std::max(stats.max_in_flight, busy);
     stats.bytes_in_use = in_use;
     stats.peak_bytes = std::max(stats.peak_bytes, in_use);

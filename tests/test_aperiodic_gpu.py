@@ -334,3 +334,29 @@ def test_cluster_schedule_rejects_grids_too_large():
     with pytest.raises(StencilError):
         plan.run(g, 10)
     plan.close()
+
+
+@pytest.mark.parametrize("dims,r,T", [((512, 512), 1, 300), ((64, 64, 64), 1, 40), ((4096,), 2, 700)])
+def test_prepared_T_runs_without_allocating(dims, r, T):
+    # after stencil_prepare the first run for T allocates no device memory (the
+    # free-memory figure does not move) and matches the loop
+    from paper_2105_06676_gb300 import StencilPlan
+    w = wl.weights_random_box(len(dims), r, 12)
+    a0 = wl.grid_uniform(dims, 13)
+    # a throwaway run first, so that lazily loaded kernel code is resident
+    warm = StencilPlan(dims, w, "dirichlet", "fp32")
+    warm.run(torch.tensor(a0, dtype=torch.float32, device="cuda"), T)
+    assert warm.status() == 0
+    warm.close()
+    plan = StencilPlan(dims, w, "dirichlet", "fp32")
+    plan.prepare(T)
+    g = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    plan.run(g, T)
+    assert plan.status() == 0
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= 2e-4
+    plan.close()

@@ -115,6 +115,7 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.stencil_plan_set_schedule(None, 0) == -1
     assert lib.stencil_plan_autotune(None, None, 5, None, None, 0) == -1
     assert lib.stencil_profile_enable(None, 1) == -1
+    assert lib.stencil_prepare(None, 5, None) == -1
 
 
 def test_size_limits_and_workspace(lib):
@@ -128,6 +129,13 @@ def test_size_limits_and_workspace(lib):
     # half spectrum 4096 x (2048 + 1 padded to 2064) complex float
     assert lib.stencil_workspace_bytes(2, d, 1, 0, 1) == 4096 * 2064 * 8
     d1 = (ctypes.c_int64 * 1)(4096)
-    assert lib.stencil_workspace_bytes(1, d1, 1, 0, 0) == 0
+    # 1-D periodic FP64 held by one CTA: no half spectrum, the (2048 + 1)-entry
+    # multiplier table kept for a repeated T; zero Dirichlet keeps no such table
+    assert lib.stencil_workspace_bytes(1, d1, 1, 0, 0) == 2049 * 16
+    assert lib.stencil_workspace_bytes(1, d1, 1, 1, 0) == 0
+    # 3-D periodic FP32: half spectrum plus the table laid out like it
+    d3 = (ctypes.c_int64 * 3)(64, 32, 128)
+    assert lib.stencil_workspace_bytes(3, d3, 1, 0, 1) == 2 * 64 * 32 * 80 * 8
+    assert lib.stencil_workspace_bytes(3, d3, 1, 1, 1) == 64 * 32 * 80 * 8
     assert lib.stencil_profile_kind_name(0).decode() == "rows_r2c"
     assert lib.stencil_profile_kind_name(999) is None

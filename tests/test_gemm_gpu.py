@@ -75,3 +75,32 @@ def test_gemm_rejects_unsupported_shapes():
             StencilPlan(dims, w2, boundary, "fp32_gemm_bf16")
     with pytest.raises(StencilError):
         StencilPlan((4096,), np.array([0.25, 0.5, 0.25]), "periodic", "fp32_gemm_bf16")
+
+
+def test_abandoned_tensor_core_wait_reports_timeout_and_plan_recovers(monkeypatch):
+    # With the test hook the tensor-core kernel issues no MMA, so its first
+    # bounded wait runs out (about 2 s): the CTA records the timeout, issues and
+    # waits on nothing more, releases its tensor memory and returns. The host
+    # reads STENCIL_ETIMEOUT; the context stays usable and the next solve (hook
+    # off) is correct.
+    import time
+    from paper_2105_06676_gb300 import StencilPlan
+    dims, T = (256, 64), 30           # 3 CTAs: every one of them times out once
+    w = wl.weights_star(2, 0.6, 0.1)
+    a0 = wl.grid_uniform(dims, 3)
+    plan = StencilPlan(dims, w, "periodic", "fp32_gemm_bf16x3")
+    g = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    monkeypatch.setenv("STENCILFFT_TEST_SKIP_MMA_COMMIT", "1")
+    t0 = time.perf_counter()
+    plan.run(g, T)
+    rc = plan.status()
+    elapsed = time.perf_counter() - t0
+    monkeypatch.delenv("STENCILFFT_TEST_SKIP_MMA_COMMIT")
+    assert rc == -4, rc               # STENCIL_ETIMEOUT
+    assert elapsed < 30.0
+    g = torch.tensor(a0, dtype=torch.float32, device="cuda")
+    plan.run(g, T)
+    assert plan.status() == 0
+    ref = oracle.stencil_loop(a0, w, T)
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= BOUND["fp32_gemm_bf16x3"]
+    plan.close()

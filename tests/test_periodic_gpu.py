@@ -363,3 +363,24 @@ def test_long_strided_axes_repeated_T_and_large_T(dims):
         assert plan.status() == 0
         assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL["fp32"]
     plan.close()
+
+
+@pytest.mark.parametrize("dims,precision", [((64, 32, 128), "fp32"), ((4096,), "fp64"),
+                                            ((256, 128), "fp32")])
+def test_prepared_T_first_run_uses_the_table_and_matches(dims, precision):
+    # stencil_prepare builds the multiplier table for T (3-D, one-CTA 1-D) ahead
+    # of time: the first run then reads it; the result is the one an unprepared
+    # run gives, within the tolerance, and matches the loop
+    from paper_2105_06676_gb300 import StencilPlan
+    w = weights_for(len(dims), "asym", 1, 8)
+    a0 = wl.grid_uniform(dims, 31)
+    T = 57
+    ref = oracle.stencil_loop(a0, w, T)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plan = StencilPlan(dims, w, "periodic", precision)
+    plan.prepare(T)
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan.run(g, T)
+    assert plan.status() == 0
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
+    plan.close()

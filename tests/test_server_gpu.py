@@ -127,3 +127,39 @@ def test_queue_full_and_invalid_requests():
     tiny = torch.rand((2, 8), dtype=torch.float32, device="cuda")
     assert srv.try_submit(tiny, wl.weights_star(2, 0.6, 0.1), 5)[0] == -1  # axis below 4
     srv.close()                              # drains what was queued
+
+
+def test_submit_returns_while_an_eviction_waits_for_running_work():
+    # Plan eviction runs on the worker without the server lock and without a
+    # device-wide synchronisation, so a submit made while the worker evicts an
+    # idle plan (next to a long solve in flight) returns at once.
+    # Budget (server estimates): A = 8192^2 FP32 zero-Dirichlet 2.955e9 B,
+    # C = 4096^2 FP32 periodic 6.80e7 B, B = 8192^2 FP32 periodic 2.70e8 B:
+    # A + C fit 3.1e9, adding B evicts the idle C (and B then waits for A).
+    import time
+    from paper_2105_06676_gb300 import StencilServer
+    srv = StencilServer(hbm_budget_bytes=3_100_000_000, max_slots=4)
+    w5 = wl.weights_star(2, 0.6, 0.1)
+    gc = torch.rand((4096, 4096), dtype=torch.float32, device="cuda")
+    ga = torch.rand((8192, 8192), dtype=torch.float32, device="cuda")
+    gb = torch.rand((8192, 8192), dtype=torch.float32, device="cuda")
+    gd = torch.rand((64, 64), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    tc = srv.submit(gc, w5, 100, "periodic")
+    assert srv.wait(tc, 60.0)[0] == 0                  # C's plan is now idle in the pool
+    ta = srv.submit(ga, wl.weights_random_box(2, 1, 4), 100000, "dirichlet")
+    t0 = time.perf_counter()
+    while srv.stats()["max_in_flight"] < 1 and time.perf_counter() - t0 < 60:
+        time.sleep(0.01)
+    time.sleep(0.3)
+    tb = srv.submit(gb, w5, 100, "periodic")           # the worker evicts C for B
+    time.sleep(0.2)
+    t1 = time.perf_counter()
+    td = srv.submit(gd, w5, 10, "periodic")
+    submit_s = time.perf_counter() - t1
+    a_done = srv.poll(ta)[0]
+    assert not a_done, "the long solve finished too early for this test"
+    assert submit_s < 0.1, submit_s
+    for t in (ta, tb, td):
+        assert srv.wait(t, 300.0)[0] == 0
+    srv.close()

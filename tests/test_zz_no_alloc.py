@@ -54,13 +54,19 @@ def _planned(a0, w, T, precision):
     return g.double().cpu().numpy()
 
 
+CALLS = [
+    ((512, 256), wl.weights_star(2, 0.6, 0.1), 1000, "fp32"),
+    ((128, 256), wl.weights_random_box(2, 2, 3), 77, "fp64"),
+    ((4096,), wl.weights_1d([0.25, 0.5, 0.25]), 1000, "fp64"),     # 1-D: no half-spectrum scratch
+    ((64, 64, 64), wl.weights_star(3, 0.4, 0.1), 200, "fp32"),     # 3-D: three passes per direction
+]
+
+
 def test_noalloc_matches_planned_run_twice():
+    # two calls in a row on each shape (the array keeps the previous call's
+    # contents), each against stencil_plan + stencil_run
     lib = _lib()
-    calls = [
-        ((512, 256), wl.weights_star(2, 0.6, 0.1), 1000, "fp32"),
-        ((128, 256), wl.weights_random_box(2, 2, 3), 77, "fp64"),
-    ]
-    for dims, w, T, precision in calls:
+    for dims, w, T, precision in CALLS + CALLS:
         a0 = wl.grid_uniform(dims, 11 + T)
         dt = torch.float32 if precision == "fp32" else torch.float64
         g = torch.tensor(a0, dtype=dt, device="cuda")
@@ -70,6 +76,24 @@ def test_noalloc_matches_planned_run_twice():
         ref = _planned(a0, w, T, precision)
         err = np.max(np.abs(got - ref)) / np.max(np.abs(a0))
         assert err <= TOL[precision], (dims, precision, err)
+
+
+def test_noalloc_calls_leave_free_device_memory_unchanged():
+    # after one call per shape (kernel code loaded), further calls of every shape
+    # take no device memory: the free-memory figure does not move
+    lib = _lib()
+    grids = []
+    for dims, w, T, precision in CALLS:
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        g = torch.tensor(wl.grid_uniform(dims, 5), dtype=dt, device="cuda")
+        assert _noalloc(lib, g, w, T, precision) == 0
+        grids.append(g)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for g, (dims, w, T, precision) in zip(grids, CALLS):
+        assert _noalloc(lib, g, w, T + 1, precision) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
