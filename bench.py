@@ -224,14 +224,25 @@ def time_solve(plan, grid, pristine, flush, K, W, T):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
-def serve_mixed_stream(n_requests: int, seed: int = 5000):
+def serve_mixed_stream(n_requests: int, loads=(0.5, 0.8, 0.95), seed: int = 5000,
+                       fp64_sample=None, oracle_sample: int = 8, workers: int = 1,
+                       oracle_max_updates: float = 2e8):
     """Mixed solve stream through the server (FP32 passes, FP64 Lambda^T).
 
-    Sizes as drawn for the serving configuration: 1-D l = 2^U{12..24}, 2-D per-axis
-    2^U{6..13}, 3-D per-axis 2^U{4..8}; T log-uniform in [10, 1e5]; boundary 50/50;
-    radius 1-2 box with random weights summing to 1. First the capacity (all
-    requests queued at once), then a Poisson replay at 0.8x that rate for
-    p50/p99 latency, then the plain FP64 one-request-at-a-time path.
+    Requests as drawn for the serving configuration: 1-D l = 2^U{12..24}, 2-D
+    per-axis 2^U{6..13}, 3-D per-axis 2^U{4..8}; T = floor(10^U[1,5]); boundary
+    50/50; radius 1-2 box with random weights summing to 1; seed 5000.
+      * capacity: every request queued at once (after a warm-up request per
+        plan shape), its results checked;
+      * each load in `loads`: Poisson arrivals at that fraction of the measured
+        capacity; p50 / p99 submit-to-completion latency over every request;
+      * the plain FP64 path one request at a time on cached, warmed plans (a
+        plan per shape, stencil_plan_set_weights per request, the per-T set-up
+        done by stencil_prepare outside the timed region), on every request or
+        on a seeded sample of `fp64_sample`; each of those requests' served FP32
+        result is compared with its FP64 result;
+      * a seeded sample of requests with N*T <= oracle_max_updates is compared
+        with the FP64 loop oracle.
     """
     import threading
 
@@ -242,24 +253,25 @@ def serve_mixed_stream(n_requests: int, seed: int = 5000):
     from paper_2105_06676_gb300 import workloads as wl
 
     reqs = wl.mixed_stream(n_requests, 1.0, seed)
-    inputs = [torch.tensor(wl.grid_uniform(r.dims, r.grid_seed), dtype=torch.float32, device="cuda")
-              for r in reqs]
-    updates = sum(int(np.prod(r.dims)) * r.T for r in reqs)
+    grids = [torch.tensor(wl.grid_uniform(r.dims, r.grid_seed), dtype=torch.float32, device="cuda")
+             for r in reqs]
+    torch.cuda.synchronize()
+    cells = [int(np.prod(r.dims)) for r in reqs]
+    updates = sum(c * r.T for c, r in zip(cells, reqs))
 
-    def run_server(arrivals):
-        grids = [x.clone() for x in inputs]
-        torch.cuda.synchronize()
+    def run_server(idx, arrivals):
         srv = StencilServer(hbm_budget_bytes=64 << 30, max_slots=8, queue_capacity=1 << 20)
-        tickets = [None] * len(reqs)
+        tickets = [None] * len(idx)
 
         def producer():
             t0 = time.perf_counter()
-            for i, r in enumerate(reqs):
+            for n, i in enumerate(idx):
                 if arrivals is not None:
-                    delay = arrivals[i] - (time.perf_counter() - t0)
+                    delay = arrivals[n] - (time.perf_counter() - t0)
                     if delay > 0:
                         time.sleep(delay)
-                tickets[i] = srv.submit(grids[i], r.weights, r.T, r.boundary)
+                r = reqs[i]
+                tickets[n] = srv.submit(grids[i], r.weights, r.T, r.boundary)
 
         t0 = time.perf_counter()
         th = threading.Thread(target=producer)
@@ -267,7 +279,7 @@ def serve_mixed_stream(n_requests: int, seed: int = 5000):
         th.join()
         lats = []
         for t in tickets:
-            rc, lat = srv.wait(t, 600.0)
+            rc, lat = srv.wait(t, 3600.0)
             assert rc == 0, rc
             lats.append(lat)
         wall = time.perf_counter() - t0
@@ -275,34 +287,96 @@ def serve_mixed_stream(n_requests: int, seed: int = 5000):
         srv.close()
         return wall, np.array(lats), st
 
-    # warm the plan pool, then measure capacity with everything queued at once
-    run_server(None)
-    wall_cap, lat_cap, st = run_server(None)
-    rate = 0.8 * len(reqs) / wall_cap
-    rng = np.random.default_rng(seed + 1)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    wall, lats, st = run_server(arrivals)
-
-    # plain FP64 path, one request at a time (plan, solve, synchronise)
-    grids64 = [x.double() for x in inputs]
+    # warm-up: one request per plan shape (the server's plan pool starts empty
+    # in every run; this loads kernels and sizes the process's memory pools)
+    seen, warm = set(), []
+    for i, r in enumerate(reqs):
+        key = (r.dims, r.boundary, r.weights.shape[0])
+        if key not in seen:
+            seen.add(key)
+            warm.append(i)
+    run_server(warm, None)
+    for i in warm:   # fresh inputs again for the checked capacity pass
+        grids[i].copy_(torch.tensor(wl.grid_uniform(reqs[i].dims, reqs[i].grid_seed),
+                                    dtype=torch.float32))
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for g, r in zip(grids64, reqs):
-        plan = StencilPlan(r.dims, r.weights, r.boundary, "fp64")
-        plan.run(g, r.T)
+
+    everyone = list(range(len(reqs)))
+    wall_cap, lat_cap, st_cap = run_server(everyone, None)
+    capacity = len(reqs) / wall_cap
+
+    # checks of the capacity pass's results (the load passes below reuse the grids)
+    rng = np.random.default_rng(seed + 7)
+    sample = everyone if fp64_sample is None or fp64_sample >= len(reqs) else \
+        sorted(rng.choice(len(reqs), size=fp64_sample, replace=False).tolist())
+    plans64 = {}
+    worst64, t64, upd64 = 0.0, 0.0, 0
+    for i in sample:
+        r = reqs[i]
+        key = (r.dims, r.boundary)
+        if key not in plans64:
+            plans64[key] = StencilPlan(r.dims, r.weights, r.boundary, "fp64")
+            warm_g = torch.zeros(r.dims, dtype=torch.float64, device="cuda")
+            plans64[key].run(warm_g, 1)
+            del warm_g
+        plan = plans64[key]
+        plan.set_weights(r.weights)
+        a0 = torch.tensor(wl.grid_uniform(r.dims, r.grid_seed), dtype=torch.float64, device="cuda")
+        amax = float(a0.abs().max())
+        plan.prepare(r.T)
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.run(a0, r.T)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t0
+        upd64 += cells[i] * r.T
+        assert plan.status() == 0
+        worst64 = max(worst64, float((grids[i].double() - a0).abs().max()) / amax)
+        del a0
+    for plan in plans64.values():
         plan.close()
-    wall64 = time.perf_counter() - t0
+    ora = []
+    small = [i for i in everyone if cells[i] * reqs[i].T <= oracle_max_updates]
+    if small and oracle_sample > 0:
+        import oracle
+        pick = sorted(rng.choice(len(small), size=min(oracle_sample, len(small)), replace=False))
+        for j in pick:
+            r = reqs[small[j]]
+            a0 = wl.grid_uniform(r.dims, r.grid_seed)
+            ref = oracle.stencil_loop(a0, r.weights, r.T, r.boundary)
+            got = grids[small[j]].double().cpu().numpy()
+            ora.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(a0))))
+
+    per_load = {}
+    for n, frac in enumerate(loads):
+        rate = frac * capacity
+        arr = np.cumsum(np.random.default_rng(seed + 1 + n).exponential(1.0 / rate, size=len(reqs)))
+        wall, lats, st = run_server(everyone, arr)
+        per_load[str(frac)] = {
+            "rate_req_per_s": rate, "wall_s": wall,
+            "p50_ms": float(np.percentile(lats, 50) * 1e3),
+            "p99_ms": float(np.percentile(lats, 99) * 1e3),
+            "latencies": int(lats.size),
+            "point_updates_per_s": updates / wall,
+            "batched_requests": st["batched_requests"], "max_in_flight": st["max_in_flight"]}
+    del grids
+    torch.cuda.synchronize()
     return {
         "requests": len(reqs), "updates": updates,
-        "capacity_req_per_s": len(reqs) / wall_cap,
+        "capacity_req_per_s": capacity,
         "value": updates / wall_cap, "unit": "point-updates/s",
-        "poisson_rate_req_per_s": rate,
-        "p50_ms": float(np.percentile(lats, 50) * 1e3), "p99_ms": float(np.percentile(lats, 99) * 1e3),
-        "poisson_point_updates_per_s": updates / wall,
-        "fp64_one_at_a_time": {"value": updates / wall64, "wall_s": wall64},
-        "max_in_flight": st["max_in_flight"], "batched_launches": st["batched_launches"],
-        "batched_requests": st["batched_requests"],
+        "capacity_p50_ms": float(np.percentile(lat_cap, 50) * 1e3),
+        "capacity_p99_ms": float(np.percentile(lat_cap, 99) * 1e3),
+        "loads": per_load,
+        "fp64_one_at_a_time": {
+            "requests": len(sample), "value": upd64 / t64 if t64 else None,
+            "seconds_in_runs": t64,
+            "plans": "cached per shape, weights set per request, per-T set-up outside the timing"},
+        "err_vs_fp64_path_max": worst64, "err_vs_fp64_path_requests": len(sample),
+        "err_vs_oracle_max": max(ora) if ora else None, "err_vs_oracle_requests": len(ora),
+        "tolerance": 2e-4,
+        "max_in_flight": st_cap["max_in_flight"], "batched_launches": st_cap["batched_launches"],
+        "batched_requests": st_cap["batched_requests"],
         "sizes": "1-D 2^12..2^24, 2-D 2^6..2^13 per axis, 3-D 2^4..2^8 per axis",
     }
 
@@ -358,7 +432,13 @@ def main():
     ap.add_argument("--ref-steps-per-sample", type=int, default=100)
     ap.add_argument("--cpu-sample-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
+                    help="Poisson loads as fractions of the measured serving capacity")
+    ap.add_argument("--serve-fp64-sample", type=int, default=60,
+                    help="requests (seeded sample) run on the FP64 one-at-a-time path and checked")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run the serving measurement alone and print its JSON (long streams)")
     ap.add_argument("--no-dirichlet", action="store_true",
                     help="skip the zero-Dirichlet secondary measurement (short profiling runs)")
     ap.add_argument("--no-oracle", action="store_true",
@@ -387,6 +467,15 @@ def main():
     from paper_2105_06676_gb300 import workloads as wl
 
     workers = os.cpu_count() or 1
+    if args.serve_only:
+        with ClockSampler(local) as clk_s:
+            serving = serve_mixed_stream(args.serve_requests,
+                                         tuple(float(x) for x in args.serve_loads.split(",")),
+                                         fp64_sample=args.serve_fp64_sample, workers=workers)
+        serving["clocks"] = clk_s.summary()
+        if rank == 0:
+            print(json.dumps({"serving": serving}), flush=True)
+        return 0
     check = not args.no_oracle
     if check:
         import oracle
@@ -559,7 +648,10 @@ def main():
         del outd
 
     # ---- serving: mixed stream through the continuous-batching server
-    serving = serve_mixed_stream(args.serve_requests) if args.serve_requests > 0 else None
+    serving = (serve_mixed_stream(args.serve_requests,
+                                  tuple(float(x) for x in args.serve_loads.split(",")),
+                                  fp64_sample=args.serve_fp64_sample, workers=workers)
+               if args.serve_requests > 0 else None)
 
     # ---- e2e through the C ABI with pinned host buffers (H2D + solve + D2H per step)
     host_in = torch.tensor(a0, dtype=torch.float32).pin_memory()

@@ -164,6 +164,19 @@ int stencil_symbol_power(stencil_plan_t plan, int64_t T, void* out, void* stream
 int stencil_status(stencil_plan_t plan, void* stream);
 
 /*
+ * Replace the plan's stencil: radius r (0..3, every axis >= 2r+1) and
+ * (2r+1)^ndim weights (host, copied; finite), as in stencil_plan. Runs
+ * enqueued afterwards use them; runs already enqueued keep the stencil they
+ * were launched with. The plan keeps its tables and workspace; cached graphs,
+ * the repeated-T multiplier table and, when the radius changes, the
+ * zero-Dirichlet schedules (this waits for the device) are dropped. Serves a
+ * caller that solves many stencils of one grid shape (paper Sec. 4: the
+ * stencil enters only through the symbol Lambda). Returns STENCIL_OK or
+ * STENCIL_EINVAL.
+ */
+int stencil_plan_set_weights(stencil_plan_t plan, int radius, const double* weights);
+
+/*
  * Base-case cutoff of RecursiveBoundary for zero-Dirichlet plans (paper
  * Fig. "stencil-fft-algorithm-1D-aperiodic", Base Case): subproblems with
  * T < cutoff are advanced by the direct loop. cutoff >= 2, or 0 for the
@@ -335,6 +348,11 @@ int stencil_destroy(stencil_plan_t plan);
 
 /* Static, human-readable name of a status code. */
 const char* stencil_strerror(int code);
+
+/* Name of the CUDA runtime error behind the calling thread's most recent
+ * STENCIL_ECUDA or STENCIL_ENOMEM ("cudaSuccess" if there was none): a
+ * diagnostic for the caller, static storage. */
+const char* stencil_cuda_error_name(void);
 
 /*
  * Largest supported axis length for (ndim, precision, axis). axis 0..ndim-1.

@@ -36,9 +36,11 @@ SIGNATURES = [
     ("stencil_run_host", _c.c_int, [_vp, _vp, _vp, _c.c_int64, _vp]),
     ("stencil_symbol_power", _c.c_int, [_vp, _c.c_int64, _vp, _vp]),
     ("stencil_prepare", _c.c_int, [_vp, _c.c_int64, _vp]),
+    ("stencil_plan_set_weights", _c.c_int, [_vp, _c.c_int, _c.POINTER(_c.c_double)]),
     ("stencil_status", _c.c_int, [_vp, _vp]),
     ("stencil_destroy", _c.c_int, [_vp]),
     ("stencil_strerror", _c.c_char_p, [_c.c_int]),
+    ("stencil_cuda_error_name", _c.c_char_p, []),
     ("stencil_max_axis", _c.c_int64, [_c.c_int, _c.c_int, _c.c_int]),
     ("stencil_workspace_bytes", _c.c_size_t, [_c.c_int, _i64p, _c.c_int, _c.c_int, _c.c_int]),
     ("stencil_plan_set_cutoff", _c.c_int, [_vp, _c.c_int64]),
@@ -108,4 +110,7 @@ def lib():
 
 def check(code: int, where: str) -> None:
     if code != 0:
+        if code in (-2, -3):   # ENOMEM / ECUDA: name the CUDA error behind it
+            cuda = lib().stencil_cuda_error_name()
+            where = f"{where} [{cuda.decode() if cuda else '?'}]"
         raise StencilError(code, where)

@@ -67,6 +67,19 @@ class StencilPlan:
     def handle(self):
         return self._handle
 
+    def set_weights(self, weights) -> None:
+        """Replace the stencil, keeping the plan's tables and workspace
+        (stencil_plan_set_weights)."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.ndim != len(self.dims) or len(set(w.shape)) != 1 or w.shape[0] % 2 != 1:
+            raise ValueError("weights must have shape (2r+1,)*ndim")
+        r = (w.shape[0] - 1) // 2
+        _capi.check(_capi.lib().stencil_plan_set_weights(
+            self._handle, r, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "stencil_plan_set_weights")
+        self.radius = r
+        self.weights = w
+
     def set_cutoff(self, cutoff: int) -> None:
         _capi.check(_capi.lib().stencil_plan_set_cutoff(self._handle, int(cutoff)),
                     "stencil_plan_set_cutoff")

@@ -1953,6 +1953,7 @@ int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s) {
                           ? aperiodic_impl<float>(p, static_cast<float*>(grid), T, s)
                           : aperiodic_impl<double>(p, static_cast<double*>(grid), T, s);
     if (err == cudaSuccess) return STENCIL_OK;
+    note_cuda_error(err);
     if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
     if (err == cudaErrorInvalidValue) return STENCIL_EUNSUPPORTED;
     return STENCIL_ECUDA;
@@ -1963,6 +1964,7 @@ int aperiodic_prepare(stencil_plan_s* p, int64_t T) {
     Schedule* sc = nullptr;
     const cudaError_t err = prepare_all(p, T, &sc);
     if (err == cudaSuccess) return STENCIL_OK;
+    note_cuda_error(err);
     if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
     if (err == cudaErrorInvalidValue) return STENCIL_EUNSUPPORTED;
     return STENCIL_ECUDA;

@@ -379,11 +379,22 @@ SFFT_SOLVE_INST(double)
 
 }  // namespace sfft
 
+namespace sfft {
+// The CUDA error behind the calling thread's last STENCIL_ECUDA / ENOMEM.
+static thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+void note_cuda_error(cudaError_t err) {
+    if (err != cudaSuccess) t_last_cuda_error = err;
+}
+}  // namespace sfft
+
 static int from_cuda(cudaError_t err) {
     if (err == cudaSuccess) return STENCIL_OK;
+    note_cuda_error(err);
     if (err == cudaErrorMemoryAllocation) return STENCIL_ENOMEM;
     return STENCIL_ECUDA;
 }
+
+extern "C" const char* stencil_cuda_error_name(void) { return cudaGetErrorName(t_last_cuda_error); }
 
 static void free_plan(stencil_plan_s* p) {
     if (!p) return;
@@ -707,6 +718,20 @@ void plan_set_weights(stencil_plan_s* p, int radius, const double* w) {
     aperiodic_forget_graphs(p);
 }
 }  // namespace sfft
+
+extern "C" int stencil_plan_set_weights(stencil_plan_t p, int radius, const double* weights) {
+    if (!p || !weights || radius < 0 || radius > kMaxRadius) return STENCIL_EINVAL;
+    int nw = 1;
+    for (int a = 0; a < p->ndim; ++a) {
+        if (p->dims[a] < 2 * radius + 1) return STENCIL_EINVAL;
+        nw *= 2 * radius + 1;
+    }
+    for (int i = 0; i < nw; ++i)
+        if (!std::isfinite(weights[i])) return STENCIL_EINVAL;
+    if (radius != p->radius) aperiodic_forget_schedules(p);   // the schedule depends on sigma
+    plan_set_weights(p, radius, weights);
+    return STENCIL_OK;
+}
 
 extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     if (!p || (cutoff != 0 && cutoff < 2)) return STENCIL_EINVAL;

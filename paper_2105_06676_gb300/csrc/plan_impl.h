@@ -88,6 +88,8 @@ struct stencil_plan_s {
 };
 
 namespace sfft {
+// Records err as the calling thread's last CUDA error (stencil_cuda_error_name).
+void note_cuda_error(cudaError_t err);
 // Frees a plan none of whose work is still in flight, without a device-wide
 // synchronisation (stencil_destroy waits for the whole device).
 void plan_free_idle(stencil_plan_s* p);

@@ -116,9 +116,12 @@ int64_t cells_of(const stencil_request& r) {
 }
 
 bool batchable(const stencil_request& r) {
-    // the batched path needs the register kernels (last axis >= 32) and tables
+    // the batched path needs the register kernels (last axis >= 32) and
+    // per-item tables; a 1-D row must fit one CTA (longer rows take the
+    // n1 x n2 passes, which evaluate their multiplier per element)
+    const int64_t one_cta = 2 * 16 * (r.precision == STENCIL_FP32 ? kMaxThreadsF32 : kMaxThreadsF64);
     return r.boundary == STENCIL_PERIODIC && cells_of(r) <= kBatchMaxCells &&
-           r.dims[r.ndim - 1] >= 32;
+           r.dims[r.ndim - 1] >= 32 && (r.ndim != 1 || r.dims[0] <= one_cta);
 }
 
 Key key_of(const stencil_request& r, bool batch) {

@@ -116,6 +116,7 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.stencil_plan_autotune(None, None, 5, None, None, 0) == -1
     assert lib.stencil_profile_enable(None, 1) == -1
     assert lib.stencil_prepare(None, 5, None) == -1
+    assert lib.stencil_plan_set_weights(None, 1, None) == -1
 
 
 def test_size_limits_and_workspace(lib):

@@ -384,3 +384,22 @@ def test_prepared_T_first_run_uses_the_table_and_matches(dims, precision):
     assert plan.status() == 0
     assert err_rel(g.double().cpu().numpy(), ref, a0) <= TOL[precision]
     plan.close()
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "dirichlet"])
+def test_set_weights_reuses_the_plan(boundary):
+    # one plan, several stencils (including a radius change): each run matches
+    # a fresh plan's loop result
+    from paper_2105_06676_gb300 import StencilPlan
+    dims = (64, 128)
+    a0 = wl.grid_uniform(dims, 71)
+    plan = StencilPlan(dims, wl.weights_random_box(2, 1, 1), boundary, "fp64")
+    for i, r in enumerate((1, 2, 1)):
+        w = wl.weights_random_box(2, r, 80 + i)
+        plan.set_weights(w)
+        g = torch.tensor(a0, dtype=torch.float64, device="cuda")
+        plan.run(g, 37)
+        assert plan.status() == 0
+        ref = oracle.stencil_loop(a0, w, 37, boundary)
+        assert err_rel(g.cpu().numpy(), ref, a0) <= TOL["fp64"]
+    plan.close()

@@ -163,3 +163,23 @@ def test_submit_returns_while_an_eviction_waits_for_running_work():
     for t in (ta, tb, td):
         assert srv.wait(t, 300.0)[0] == 0
     srv.close()
+
+
+@pytest.mark.parametrize("L,precision", [(1 << 16, "fp32"), (1 << 15, "fp64"), (1 << 15, "fp32")])
+def test_small_1d_requests_longer_than_one_cta_are_served(L, precision):
+    # 1-D rows beyond one CTA (FP32 above 2^15 points, FP64 above 2^14) are small
+    # enough to batch by cell count but take the n1 x n2 passes: served one by one
+    from paper_2105_06676_gb300 import StencilServer
+    srv = StencilServer(hbm_budget_bytes=4 << 30, max_slots=4)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    a0s = [wl.grid_uniform((L,), 60 + i) for i in range(4)]
+    ws = [wl.weights_random_box(1, 1 + i % 2, 70 + i) for i in range(4)]
+    gs = [torch.tensor(a, dtype=dt, device="cuda") for a in a0s]
+    torch.cuda.synchronize()
+    ts = [srv.submit(g, w, 50 + i, "periodic") for i, (g, w) in enumerate(zip(gs, ws))]
+    for t in ts:
+        assert srv.wait(t, 60.0)[0] == 0
+    srv.close()
+    for i, (g, a0, w) in enumerate(zip(gs, a0s, ws)):
+        ref = oracle.stencil_loop(a0, w, 50 + i)
+        assert np.max(np.abs(g.double().cpu().numpy() - ref)) / np.max(np.abs(a0)) <= TOL[precision]
