@@ -585,8 +585,8 @@ __device__ __noinline__ void multiply_survivors_1d(View sm, int j, int q, unsign
         const int r = __ffs(mask) - 1;
         mask &= mask - 1;
         const int k[3] = {row + n1 * (j + q * r), 0, 0};
-        const double2 v = lambda_pow64(p, k);
-        const C V{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+        const double2 v = cscale_rn(lambda_pow64(p, k), p.scale);
+        const C V{(R)v.x, (R)v.y};
         C& e = sm[j + q * r];
         e = cmul(e, V);
     }

@@ -124,32 +124,133 @@ __device__ __forceinline__ C lambda_eval(const SymbolParams& p, const C* const* 
     }
 }
 
+// FP64 complex arithmetic with every rounding spelled out (no contraction left
+// to the compiler), so that every kernel that evaluates a multiplier -- inside a
+// pass or into a table -- produces the same bits.
+__device__ __forceinline__ double2 cmul_rn(double2 a, double2 b) {
+    return double2{__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x))};
+}
+__device__ __forceinline__ double2 cadd_rn(double2 a, double2 b) {
+    return double2{__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)};
+}
+__device__ __forceinline__ double2 cscale_rn(double2 a, double s) {
+    return double2{__dmul_rn(a.x, s), __dmul_rn(a.y, s)};
+}
+
 // z^T by repeated squaring over the bits of T (T >= 0).
 __device__ __forceinline__ double2 cpow_sq(double2 z, long long T) {
     double2 v{1.0, 0.0};
     double2 s = z;
     while (T > 0) {
-        if (T & 1) v = cmul(v, s);
+        if (T & 1) v = cmul_rn(v, s);
         T >>= 1;
-        if (T > 0) s = cmul(s, s);
+        if (T > 0) s = cmul_rn(s, s);
     }
     return v;
 }
 __device__ __forceinline__ double rpow_sq(double x, long long T) {
     double v = 1.0, s = x;
     while (T > 0) {
-        if (T & 1) v *= s;
+        if (T & 1) v = __dmul_rn(v, s);
         T >>= 1;
-        if (T > 0) s *= s;
+        if (T > 0) s = __dmul_rn(s, s);
     }
     return v;
 }
 
-// Lambda[k]^T in FP64 (no scale, no shortcut).
-static __device__ __noinline__ double2 lambda_pow64(const SymbolParams& p, const int* k) {
-    const double2 lam = lambda_eval<double, double2>(p, p.E64, p.w, k);
+// FP64 factorisation of Lambda along axis 0 for fixed k_1, k_2:
+// G64[m_0] = sum_{m_1..} w[m_0, m_1, ..] prod_{a >= 1} E64_a[m_a k_a], so that
+// Lambda(k) = sum_{m_0} E64_0[m_0 k_0] G64[m_0]. A column pass forms it once
+// per thread and reuses it for every element of the column it evaluates.
+template <int RAD>
+struct ColSymbol64 {
+    double2 g[2 * RAD + 1];
+};
+
+template <int RAD>
+__device__ __forceinline__ void col_symbol_init64(const SymbolParams& p, int k1, int k2,
+                                                  ColSymbol64<RAD>& cs) {
+    constexpr int W = 2 * RAD + 1;
+    if (p.ndim == 1) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) cs.g[i] = double2{p.w[i], 0.0};
+        return;
+    }
+    double2 e1[W];
+#pragma unroll
+    for (int m = -RAD; m <= RAD; ++m)
+        e1[m + RAD] = __ldg(p.E64[1] + (((m * k1) & p.tmask[1]) << p.tshift[1]));
+    if (p.ndim == 2) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            double2 inner{0.0, 0.0};
+#pragma unroll
+            for (int jj = 0; jj < W; ++jj) inner = cadd_rn(inner, cscale_rn(e1[jj], p.w[i * W + jj]));
+            cs.g[i] = inner;
+        }
+        return;
+    }
+    double2 e2[W];
+#pragma unroll
+    for (int m = -RAD; m <= RAD; ++m)
+        e2[m + RAD] = __ldg(p.E64[2] + (((m * k2) & p.tmask[2]) << p.tshift[2]));
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        double2 mid{0.0, 0.0};
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj) {
+            double2 inner{0.0, 0.0};
+#pragma unroll
+            for (int qq = 0; qq < W; ++qq)
+                inner = cadd_rn(inner, cscale_rn(e2[qq], p.w[(i * W + jj) * W + qq]));
+            mid = cadd_rn(mid, cmul_rn(e1[jj], inner));
+        }
+        cs.g[i] = mid;
+    }
+}
+
+// Lambda at k_0 for the column of cs, in FP64.
+template <int RAD>
+__device__ __forceinline__ double2 col_lambda64(const SymbolParams& p, const ColSymbol64<RAD>& cs,
+                                                int k0) {
+    double2 lam{0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 2 * RAD + 1; ++i) {
+        const int m = i - RAD;
+        const double2 e = __ldg(p.E64[0] + (((m * k0) & p.tmask[0]) << p.tshift[0]));
+        lam = cadd_rn(lam, cmul_rn(e, cs.g[i]));
+    }
+    return lam;
+}
+
+// Lambda^T (real when the weights are symmetric: only the real part is kept).
+__device__ __forceinline__ double2 symbol_pow64(const SymbolParams& p, double2 lam) {
     if (p.real_symbol) return double2{rpow_sq(lam.x, p.T), 0.0};
     return cpow_sq(lam, p.T);
+}
+
+// V[k] = Lambda[k]^T / N in FP64 for the column of cs at k_0.
+template <int RAD>
+__device__ __forceinline__ double2 col_power64(const SymbolParams& p, const ColSymbol64<RAD>& cs,
+                                               int k0) {
+    return cscale_rn(symbol_pow64(p, col_lambda64<RAD>(p, cs, k0)), p.scale);
+}
+
+template <int RAD>
+__device__ __forceinline__ double2 lambda_pow64_r(const SymbolParams& p, const int* k) {
+    ColSymbol64<RAD> cs;
+    col_symbol_init64<RAD>(p, k[1], k[2], cs);
+    return symbol_pow64(p, col_lambda64<RAD>(p, cs, k[0]));
+}
+
+// Lambda[k]^T in FP64 (no scale, no shortcut).
+static __device__ __noinline__ double2 lambda_pow64(const SymbolParams& p, const int* k) {
+    switch (p.r) {
+        case 0: return lambda_pow64_r<0>(p, k);
+        case 1: return lambda_pow64_r<1>(p, k);
+        case 2: return lambda_pow64_r<2>(p, k);
+        default: return lambda_pow64_r<3>(p, k);
+    }
 }
 
 // V[k] = Lambda[k]^T / N rounded to the pass precision (with the exact
@@ -166,8 +267,8 @@ __device__ __forceinline__ C spectral_multiplier(const SymbolParams& p, const in
             if (lg < -p.cut) return C{(R)0, (R)0};
         }
     }
-    const double2 v = lambda_pow64(p, k);
-    return C{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+    const double2 v = cscale_rn(lambda_pow64(p, k), p.scale);
+    return C{(R)v.x, (R)v.y};
 }
 
 // Per-column part of Lambda for a pass along axis 0: with k_0 the transform
@@ -236,18 +337,20 @@ __device__ __forceinline__ float2 col_lambda32(const SymbolParams& p, const ColS
 }
 
 // Multiply the survivors (bits of mask) of a thread's 16 elements, parked in
-// shared memory at sm[spad(j + q r)], by V = Lambda^T / N in FP64 (kept out of
-// line so the caller's registers are not held across it).
-template <typename C, typename View>
+// shared memory at sm[j + q r], by V = Lambda^T / N in FP64. Kept out of line
+// so the caller's registers are not held across it; the column's FP64 factors
+// are formed once here and serve every survivor.
+template <int RAD, typename C, typename View>
 __device__ __noinline__ void multiply_survivors(View sm, int j, int q, unsigned mask,
                                                 const SymbolParams& p, int k1, int k2) {
     using R = decltype(C{}.x);
+    ColSymbol64<RAD> cs;
+    col_symbol_init64<RAD>(p, k1, k2, cs);
     while (mask) {
         const int r = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int k[3] = {j + q * r, k1, k2};
-        const double2 v = lambda_pow64(p, k);
-        const C V{(R)(v.x * p.scale), (R)(v.y * p.scale)};
+        const double2 v = col_power64<RAD>(p, cs, j + q * r);
+        const C V{(R)v.x, (R)v.y};
         C& e = sm[j + q * r];
         e = cmul(e, V);
     }
@@ -261,12 +364,30 @@ __device__ __noinline__ C multiply_single(C x, const SymbolParams& p, int k0, in
     return cmul(x, spectral_multiplier<C>(p, k));
 }
 
+// True when every element of the column described by cs is below the cut:
+// |Lambda(k_0)| <= sum_m |G[m]| for every k_0 (|E| = 1), so when that sum
+// (raised by 2^-18 for the rounding of the sum and of any per-element
+// evaluation) passes the per-element test, every element does.
+template <int RAD>
+__device__ __forceinline__ bool col_below_cut(const SymbolParams& p, const ColSymbol<RAD>& cs) {
+    if (!(p.tau2 > 0.f)) return false;
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2 * RAD + 1; ++i) b += sqrtf(cs.g[i].x * cs.g[i].x + cs.g[i].y * cs.g[i].y);
+    b *= 1.0f + 0x1p-18f;
+    return b * b < p.tau2;
+}
+
 // v[r] <- V[k] v[r] for the thread's elements k_0 = j + q r of one column whose
 // other frequencies are (k1, k2) and whose FP32 factorisation is cs. Elements
 // whose FP32 bound shows |V| below half the smallest subnormal become 0; the
 // rest get the FP64 multiplier. sm (this sequence's shared buffer) is used as
 // scratch at the thread's own positions; the caller must place a barrier
 // between this and the next use of sm by other threads.
+//
+// When the column is a full transform (16 q = l_0), E_0[m (j + q r)] =
+// E_0[m j] exp(2 pi i m r / 16): one table load per m and thread, the rest
+// exact-constant rotations (their rounding is far inside the bound delta).
 template <int RAD, typename C, typename View>
 __device__ __forceinline__ void apply_multiplier(C* v, const View& sm, int j, int q,
                                                  const SymbolParams& p, const ColSymbol<RAD>& cs,
@@ -277,17 +398,56 @@ __device__ __forceinline__ void apply_multiplier(C* v, const View& sm, int j, in
         for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], (R)p.scale);
         return;
     }
-    unsigned mask = 0;
+    if (col_below_cut<RAD>(p, cs)) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const float2 l = col_lambda32<RAD>(p, cs, j + q * r);
-        if (l.x * l.x + l.y * l.y < p.tau2) v[r] = C{(R)0, (R)0};
-        else mask |= 1u << r;
+        for (int r = 0; r < 16; ++r) v[r] = C{(R)0, (R)0};
+        return;
+    }
+    unsigned mask = 0;
+    if (RAD > 0 && q * 16 == p.len[0]) {
+        float2 e[RAD > 0 ? RAD : 1];
+#pragma unroll
+        for (int m = 1; m <= RAD; ++m)
+            e[m - 1] = __ldg(p.E32[0] + (((m * j) & p.tmask[0]) << p.tshift[0]));
+        if (p.real_symbol) {
+            // Lambda real: G[-m] = conj(G[m]), Lambda = G[0] + 2 sum_m Re(E_m G[m])
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                float l = cs.g[RAD].x;
+#pragma unroll
+                for (int m = 1; m <= RAD; ++m) {
+                    const float2 em = rot16<+1>(e[m - 1], m * r);
+                    l += 2.f * (em.x * cs.g[RAD + m].x - em.y * cs.g[RAD + m].y);
+                }
+                if (l * l < p.tau2) v[r] = C{(R)0, (R)0};
+                else mask |= 1u << r;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                float2 l = cs.g[RAD];
+#pragma unroll
+                for (int m = 1; m <= RAD; ++m) {
+                    const float2 em = rot16<+1>(e[m - 1], m * r);
+                    l = cadd(l, cmul(em, cs.g[RAD + m]));
+                    l = cadd(l, cmul(cconj(em), cs.g[RAD - m]));
+                }
+                if (l.x * l.x + l.y * l.y < p.tau2) v[r] = C{(R)0, (R)0};
+                else mask |= 1u << r;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float2 l = col_lambda32<RAD>(p, cs, j + q * r);
+            if (l.x * l.x + l.y * l.y < p.tau2) v[r] = C{(R)0, (R)0};
+            else mask |= 1u << r;
+        }
     }
     if (mask) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) sm[j + q * r] = v[r];
-        multiply_survivors<C, View>(sm, j, q, mask, p, k1, k2);
+        multiply_survivors<RAD, C, View>(sm, j, q, mask, p, k1, k2);
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = mask >> r & 1 ? sm[j + q * r] : C{(R)0, (R)0};
     }
