@@ -34,7 +34,8 @@ WORKLOAD = "star5_2d_periodic_4096x4096_T10000"
 # Kernel sources whose hash keys the DRAM traffic recorded under profiles/: a
 # traffic figure is reported only while the kernels are the ones it was taken on.
 KERNEL_SOURCES = ["periodic_kernels.cuh", "fft_ct.cuh", "fft_reg.cuh", "fft_common.cuh",
-                  "symbol.cuh", "cols_tma.cuh", "rows_tma.cuh", "periodic_f32_tma.cu"]
+                  "symbol.cuh", "cols_tma.cuh", "rows_tma.cuh", "rows_blk.cuh",
+                  "periodic_f32_tma.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_star5_2d_4096_fp32.json")
 
 

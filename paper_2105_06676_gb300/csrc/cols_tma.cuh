@@ -24,6 +24,13 @@
 //   * results go straight from registers to global memory.
 // A wait that gives up after kWaitLimitNs records kGemmTimeout (bit 2 of
 // the status word) and ends the CTA (no load is then in flight).
+//
+// Blocked half spectra (BLK = 1, 2-D solves): the row passes store the half
+// spectrum of an item as column blocks, element (row i, column k) at
+// (k / CPT) n CPT + i CPT + k mod CPT, so a tile is one contiguous 64 KB block:
+// it arrives by a single cp.async.bulk and leaves by stores that cover whole
+// 256-byte runs per warp (the row-major layout moves 16-byte pieces of 4096
+// rows both ways).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -69,6 +76,17 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
         "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
         "r"(mbar)
+        : "memory");
+}
+
+// One contiguous bulk copy (untiled) into shared memory, completing on mbar;
+// both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
         : "memory");
 }
 
@@ -163,7 +181,7 @@ __device__ __forceinline__ void tw_fft(float2* v, float2* sm, int j, const Stage
 // along axis 0 (V = Lambda^T / N, from a table or evaluated per element).
 // Tile t covers column group x = t mod gx (columns x*CPT ..), mid index
 // y = (t / gx) mod g.mid and outer index z = t / (gx g.mid), as in ColGeom.
-template <int MODE, int RAD, int LOG2N>
+template <int MODE, int RAD, int LOG2N, int BLK>
 __global__ void __launch_bounds__(kTileThreads, 2)
 k_cols_tma(float2* __restrict__ H, const __grid_constant__ CUtensorMap map,
            const __grid_constant__ ColGeom g, const float2* __restrict__ tw, int twn_log2,
@@ -189,7 +207,10 @@ k_cols_tma(float2* __restrict__ H, const __grid_constant__ CUtensorMap map,
         const int y = rest % g.mid;
         const int z = rest / g.mid;
         mbar_expect_tx(bar, kTileBytes);
-        tma_load_5d(bufa, &map, x * 2 * CPT, y, 0, 0, z, bar);
+        if constexpr (BLK)
+            bulk_load(bufa, H + (long long)z * g.os + (long long)x * kTileElems, kTileBytes, bar);
+        else
+            tma_load_5d(bufa, &map, x * 2 * CPT, y, 0, 0, z, bar);
     };
 
     if (leader) {
@@ -242,10 +263,11 @@ k_cols_tma(float2* __restrict__ H, const __grid_constant__ CUtensorMap map,
             if (vt) {
                 // multipliers shared by every solve of this shape and T
                 const float2* vb = vt + (long long)y * g.ms + i0 + c;
+                const long long vs = BLK ? g.vS : g.S;   // tables keep the row-major layout
                 if (live) {
 #pragma unroll
                     for (int r = 0; r < 16; ++r)
-                        v[r] = cmul(v[r], __ldg(vb + (long long)(j + q * r) * g.S));
+                        v[r] = cmul(v[r], __ldg(vb + (long long)(j + q * r) * vs));
                 }
             } else {
                 int k[3];
@@ -266,7 +288,13 @@ k_cols_tma(float2* __restrict__ H, const __grid_constant__ CUtensorMap map,
         } else {
             tw_fft<MODE, LOG2N, CL, 4 - CL>(v, sm, j, tws, refill);
         }
-        if (live) {
+        if constexpr (BLK) {
+            // the whole block goes back (a ragged block's extra columns are
+            // finite padding that no pass reads as data)
+            float2* dst = H + (long long)z * g.os + (long long)x * kTileElems + c;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) dst[(j + q * r) * CPT] = v[r];
+        } else if (live) {
             float2* dst = H + (long long)z * g.os + (long long)y * g.ms + i0 + c;
 #pragma unroll
             for (int r = 0; r < 16; ++r) dst[(long long)(j + q * r) * g.S] = v[r];

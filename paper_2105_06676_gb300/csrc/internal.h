@@ -30,6 +30,7 @@ struct ColGeom {
     long long ms;
     int inner_valid;
     int cols_log2;
+    long long vS = 0;   // row stride of multiplier tables where it differs from S (blocked H)
 };
 
 // Launchers (templated on the real type; instantiated for float and double).
@@ -91,6 +92,23 @@ cudaError_t launch_cols_tma(void* H, const ColGeom& g, int mode, const void* tw,
 bool rows_tma_ok(const void* grid, const void* H, long long Mp, int n_log2, int nrows);
 cudaError_t launch_rows_tma(int dir, const void* src, void* dst, long long Mp, int n_log2,
                             int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s);
+
+// Blocked half spectra of FP32 2-D solves (rows_blk.cuh, cols_tma.cuh with
+// BLK = 1): an item of 2^l0_log2 rows stores its half spectrum as column blocks
+// of 8192 values (2^(13 - l0_log2) columns x all rows). blocked_ok: the three
+// passes apply (2^9 <= l0 <= 2^12, packed row length 2^8..2^12, aligned);
+// blocked_item_elems: complex values per item (at most l0 * Mp for Mp >= n + 16).
+// launch_rows_blk: dir -1 grid rows -> blocked H, +1 blocked H -> grid rows
+// (non-finite output sets bit 0 of *status); launch_cols_tma_blk: the fused
+// forward x V x inverse pass over the blocks (g.os = item stride, g.vS = row
+// stride of multiplier tables). All return cudaErrorNotSupported when not
+// applicable.
+bool blocked_ok(const void* grid, const void* H, int l0_log2, int n_log2);
+long long blocked_item_elems(int l0_log2, int n_log2);
+cudaError_t launch_rows_blk(int dir, const void* src, void* dst, int l0_log2, int n_log2,
+                            int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s);
+cudaError_t launch_cols_tma_blk(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                                const SymbolSet& ps, int* status, cudaStream_t s);
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);

@@ -10,6 +10,7 @@
 
 #include "cols_tma.cuh"
 #include "rows_tma.cuh"
+#include "rows_blk.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -88,11 +89,11 @@ cudaError_t with_len(int l, F&& f) {
     }
 }
 
-template <int MODE, int RAD, int LOG2N>
+template <int MODE, int RAD, int LOG2N, int BLK = 0>
 cudaError_t launch_t(void* H, const ColGeom& g, const CUtensorMap& map, const void* tw,
                      int twn_log2, const SymbolSet& ps, int* status, cudaStream_t s) {
     const size_t smem = tma_smem_bytes(LOG2N);
-    auto kern = k_cols_tma<MODE, RAD, LOG2N>;
+    auto kern = k_cols_tma<MODE, RAD, LOG2N, BLK>;
     cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), smem);
     if (err != cudaSuccess) return err;
     const int cpt = 1 << tma_cols_log2(LOG2N);
@@ -156,6 +157,52 @@ cudaError_t launch_rows_tma(int dir, const void* src, void* dst, long long Mp, i
     });
 }
 
+// Blocked-layout row passes (rows_blk.cuh) for packed row length 2^n_log2 and
+// 2^cl columns per block.
+template <int L, int CL, bool R2C>
+cudaError_t launch_blk_t(const void* src, void* dst, int l0_log2, long long os, int nrows,
+                         const void* tw, int twn_log2, int* status, cudaStream_t s) {
+    const size_t smem = blk_smem(L, CL);
+    const int rpt = blk_rows(L);
+    const int grid = (nrows + rpt - 1) / rpt;
+    if (R2C) {
+        auto kern = k_rows_r2c_blk<L, CL>;
+        cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), smem);
+        if (err != cudaSuccess) return err;
+        kern<<<grid, blk_threads(L), smem, s>>>(static_cast<const float2*>(src),
+                                                static_cast<float2*>(dst), l0_log2, os, nrows,
+                                                static_cast<const float2*>(tw), twn_log2);
+    } else {
+        auto kern = k_rows_c2r_blk<L, CL>;
+        cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), smem);
+        if (err != cudaSuccess) return err;
+        kern<<<grid, blk_threads(L), smem, s>>>(static_cast<const float2*>(src),
+                                                static_cast<float2*>(dst), l0_log2, os, nrows,
+                                                static_cast<const float2*>(tw), twn_log2, status);
+    }
+    return cudaGetLastError();
+}
+
+template <int L, typename F>
+cudaError_t with_blk_len(int l, F&& f) {
+    if constexpr (L > kBlkLog2Hi) {
+        return cudaErrorNotSupported;
+    } else {
+        if (l == L) return f(std::integral_constant<int, L>{});
+        return with_blk_len<L + 1>(l, f);
+    }
+}
+
+template <int CL, typename F>
+cudaError_t with_cl(int cl, F&& f) {
+    if constexpr (CL > 4) {
+        return cudaErrorNotSupported;
+    } else {
+        if (cl == CL) return f(std::integral_constant<int, CL>{});
+        return with_cl<CL + 1>(cl, f);
+    }
+}
+
 bool cols_tma_ok(const void* H, const ColGeom& g) {
     if (!tma_enabled() || !encode_tiled() || sm_count() <= 0) return false;
     if (g.log2n < kTmaLog2Lo || g.log2n > kTmaLog2Hi) return false;
@@ -190,6 +237,65 @@ cudaError_t launch_cols_tma(void* H, const ColGeom& g, int mode, const void* tw,
             case 1: return launch_t<0, 1, L>(H, g, map, tw, twn_log2, set, status, s);
             case 2: return launch_t<0, 2, L>(H, g, map, tw, twn_log2, set, status, s);
             default: return launch_t<0, 3, L>(H, g, map, tw, twn_log2, set, status, s);
+        }
+    });
+}
+
+// STENCILFFT_BLOCKED=0 keeps row-major half spectra for 2-D solves (A/B timing).
+static bool blocked_enabled() {
+    static bool on = [] {
+        const char* e = std::getenv("STENCILFFT_BLOCKED");
+        return !(e && std::strcmp(e, "0") == 0);
+    }();
+    return on;
+}
+
+bool blocked_ok(const void* grid, const void* H, int l0_log2, int n_log2) {
+    if (!tma_enabled() || !blocked_enabled() || sm_count() <= 0) return false;
+    if (l0_log2 < kTmaLog2Lo || l0_log2 > kTmaLog2Hi) return false;
+    if (n_log2 < kBlkLog2Lo || n_log2 > kBlkLog2Hi) return false;
+    return reinterpret_cast<uintptr_t>(grid) % 16 == 0 && reinterpret_cast<uintptr_t>(H) % 16 == 0;
+}
+
+long long blocked_item_elems(int l0_log2, int n_log2) {
+    const int cl = tma_cols_log2(l0_log2);
+    const long long nx = (((long long)1 << n_log2) + 1 + (1 << cl) - 1) >> cl;
+    return nx << 13;   // nx blocks of 8192 values
+}
+
+cudaError_t launch_rows_blk(int dir, const void* src, void* dst, int l0_log2, int n_log2,
+                            int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s) {
+    const void* grid = dir < 0 ? src : dst;
+    const void* H = dir < 0 ? dst : src;
+    if (!blocked_ok(grid, H, l0_log2, n_log2) || nrows % (1 << l0_log2)) return cudaErrorNotSupported;
+    const long long os = blocked_item_elems(l0_log2, n_log2);
+    return with_blk_len<kBlkLog2Lo>(n_log2, [&](auto tl) -> cudaError_t {
+        constexpr int L = decltype(tl)::value;
+        return with_cl<1>(tma_cols_log2(l0_log2), [&](auto tc) -> cudaError_t {
+            constexpr int CL = decltype(tc)::value;
+            if (dir < 0)
+                return launch_blk_t<L, CL, true>(src, dst, l0_log2, os, nrows, tw, twn_log2,
+                                                  status, s);
+            return launch_blk_t<L, CL, false>(src, dst, l0_log2, os, nrows, tw, twn_log2, status,
+                                              s);
+        });
+    });
+}
+
+cudaError_t launch_cols_tma_blk(void* H, const ColGeom& g, const void* tw, int twn_log2,
+                                const SymbolSet& ps, int* status, cudaStream_t s) {
+    if (!tma_enabled() || sm_count() <= 0 || g.log2n < kTmaLog2Lo || g.log2n > kTmaLog2Hi ||
+        g.mid != 1 || reinterpret_cast<uintptr_t>(H) % 16)
+        return cudaErrorNotSupported;
+    CUtensorMap map;   // unused by the blocked kernels
+    std::memset(&map, 0, sizeof(map));
+    return with_len<kTmaLog2Lo>(g.log2n, [&](auto tag) -> cudaError_t {
+        constexpr int L = decltype(tag)::value;
+        switch (ps.p[0].r) {
+            case 0: return launch_t<0, 0, L, 1>(H, g, map, tw, twn_log2, ps, status, s);
+            case 1: return launch_t<0, 1, L, 1>(H, g, map, tw, twn_log2, ps, status, s);
+            case 2: return launch_t<0, 2, L, 1>(H, g, map, tw, twn_log2, ps, status, s);
+            default: return launch_t<0, 3, L, 1>(H, g, map, tw, twn_log2, ps, status, s);
         }
     });
 }

@@ -276,6 +276,30 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     }
     const int64_t rows_item = d == 2 ? len[0] : len[0] * len[1];
     const int64_t rows = rows_item * items;
+    R* out = Sout ? Sout : S;
+    if (d == 2 && sizeof(R) == 4 && p->gemm < 0) {
+        // FP32 2-D: half spectra in column blocks (rows_blk.cuh), so the fused
+        // column pass moves one contiguous 64 KB block per tile
+        const int l0_log2 = ilog2_exact(len[0]);
+        if (blocked_ok(S, H, l0_log2, n_log2) && blocked_ok(out, H, l0_log2, n_log2)) {
+            ColGeom g;
+            g.log2n = l0_log2;
+            g.S = 1ll << (13 - l0_log2);   // columns per block: rows are that far apart
+            g.outer = items;
+            g.os = blocked_item_elems(l0_log2, n_log2);
+            g.mid = 1;
+            g.ms = 0;
+            g.inner_valid = n + 1;
+            g.cols_log2 = 13 - l0_log2;
+            g.vS = Mp;
+            PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_blk(-1, S, H, l0_log2, n_log2, (int)rows, tw,
+                                                       twn_log2, status, s));
+            PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_tma_blk(H, g, tw, twn_log2, ss, status, s));
+            PROF_LAUNCH(PASS_ROWS_C2R, launch_rows_blk(+1, H, out, l0_log2, n_log2, (int)rows, tw,
+                                                       twn_log2, status, s));
+            return cudaSuccess;
+        }
+    }
     // R2C keeps the register row kernel: its bulk-copy variant measured slower
     // on GB300 (4096^2: 44 -> 48 us; 512^3: 194 -> 228 us)
     PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_r2c<R>(S, H, Mp, n_log2, (int)rows, tw, twn_log2, s));
@@ -346,7 +370,6 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     // d >= 2 reads S once (R2C) and writes the result once (C2R): Sout may be a
     // different buffer, e.g. host memory the GPU maps over the chip-to-chip link
     // C2R reads H through bulk copies (512^3: 231 -> 189 us; 4096^2: equal)
-    R* out = Sout ? Sout : S;
     if (sizeof(R) == 4 && rows_tma_ok(out, H, Mp, n_log2, (int)rows))
         PROF_LAUNCH(PASS_ROWS_C2R, launch_rows_tma(+1, H, out, Mp, n_log2, (int)rows, tw, twn_log2,
                                                    status, s));

@@ -1,0 +1,192 @@
+#pragma once
+// Contiguous-axis passes of StencilFFT-P for FP32 2-D grids that keep the half
+// spectrum in column blocks (paper Sec. 4, Fig. "stencil-fft-algorithm-dD":
+// the forward Multi-FFT along the stored-contiguous axis with the real-input
+// split, Step 1; its inverse, Step 4). The strided-axis pass between them
+// (cols_tma.cuh, BLK = 1) then reads and writes one contiguous 64 KB block per
+// tile.
+//
+// Layout: an item of l0 rows has its half spectrum X[i][k] (k = 0..n, n = l1/2)
+// at  (k >> CL) * l0 * CPT + i * CPT + (k & (CPT - 1)),  CPT = 2^CL columns per
+// block, NX = ceil((n + 1) / CPT) blocks; items follow each other every
+// NX * l0 * CPT elements. Columns n+1 .. NX*CPT-1 hold zeros.
+//
+// A CTA transforms RPT consecutive rows of one item (q = n/16 threads per row,
+// 16 elements per thread, the register FFT of fft_ct.cuh), so for every block x
+// its rows form one contiguous run of RPT * CPT values (RPT >= 2, CPT >= 2:
+// at least 32 bytes, whole sectors). The runs pass through a shared staging
+// area so that global memory sees 16-byte accesses with lane pairs covering
+// whole 32-byte sectors.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_ct.cuh"
+#include "internal.h"
+
+namespace sfft {
+
+constexpr int kBlkLog2Lo = 8, kBlkLog2Hi = 12;
+
+// Threads and rows per CTA of the blocked row passes: at least two rows, at
+// least 256 threads. (Four rows per CTA -- 64-byte runs, 512 threads for
+// 2048-point rows -- measured slower on GB300: 4096^2 R2C 53.5 -> 55.7 us, C2R
+// 49.0 -> 53.8 us.)
+__host__ __device__ constexpr int blk_threads(int log2n) {
+    return ((1 << log2n) >> 4) * 2 > 256 ? ((1 << log2n) >> 4) * 2 : 256;
+}
+__host__ __device__ constexpr int blk_rows(int log2n) {
+    return blk_threads(log2n) / ((1 << log2n) >> 4);
+}
+// Sequence stride of the exchange buffer (seq_stride of fft_common.cuh).
+__host__ __device__ constexpr int blk_seq_stride(int log2n) {
+    return (1 << log2n) + ((1 << log2n) >> 5) + 1;
+}
+__host__ __device__ constexpr int blk_nx(int log2n, int cl) {
+    return ((1 << log2n) + 1 + (1 << cl) - 1) >> cl;
+}
+__host__ __device__ constexpr size_t blk_smem(int log2n, int cl) {
+    const size_t ex = (size_t)blk_rows(log2n) * blk_seq_stride(log2n);
+    const size_t st = (size_t)blk_nx(log2n, cl) * blk_rows(log2n) * (1 << cl);
+    return (ex > st ? ex : st) * 8;
+}
+
+// Staging position of X[c][k] (row c of the CTA): block-major, rows within a
+// block, columns within a row: the order of the global runs.
+template <int CL, int RPT>
+__device__ __forceinline__ int blk_stage(int c, int k) {
+    return ((k >> CL) * RPT + c) * (1 << CL) + (k & ((1 << CL) - 1));
+}
+
+// R2C: rows of the real grid (viewed as n complex pairs) -> blocked half spectra.
+template <int LOG2N, int CL>
+__global__ void __launch_bounds__(blk_threads(LOG2N), 1024 / blk_threads(LOG2N))
+k_rows_r2c_blk(const float2* __restrict__ grid, float2* __restrict__ H, int l0_log2, long long os,
+               int nrows, const float2* __restrict__ tw, int twn_log2) {
+    constexpr int n = 1 << LOG2N, q = n >> 4;
+    constexpr int RPT = blk_rows(LOG2N), CPT = 1 << CL, NX = blk_nx(LOG2N, CL);
+    constexpr int SS = blk_seq_stride(LOG2N);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2* buf = reinterpret_cast<float2*>(smraw);
+    const int c = threadIdx.x / q, j = threadIdx.x - c * q;
+    const long long row0 = (long long)blockIdx.x * RPT;   // first row of the CTA (all items)
+    const long long row = row0 + c;
+    const bool live = row < nrows;
+    const SeqView<float2> sv{buf + c * SS};
+    const float2* rowp = grid + (live ? row : 0) * n;
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = live ? __ldg(rowp + j + q * s) : float2{0.f, 0.f};
+    ct_fft<-1, LOG2N, 0, 5>(v, buf + c * SS, j, tw, twn_log2);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) sv[j + q * r] = v[r];
+    __syncthreads();
+    // real-input split: X[k] from Z[k] and Z[n-k]
+    const int sh = twn_log2 - LOG2N - 1;   // W^k = exp(-2 pi i k / 2n) = tw[k << sh]
+    float2 xn{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = j + q * r;
+        const float2 zk = v[r], znk = sv[(n - k) & (n - 1)];
+        const float2 xe = cscale(cadd(zk, cconj(znk)), 0.5f);
+        const float2 xo = cscale(cmul_mi(csub(zk, cconj(znk))), 0.5f);
+        v[r] = cadd(xe, cmul(__ldg(tw + (k << sh)), xo));
+        if (k == 0) xn = csub(xe, xo);   // X[n] = Xe[0] - Xo[0]
+    }
+    __syncthreads();   // every partner read is done: the buffer becomes the staging area
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[blk_stage<CL, RPT>(c, j + q * r)] = v[r];
+    if (j == 0) {
+        buf[blk_stage<CL, RPT>(c, n)] = xn;
+#pragma unroll
+        for (int k = n + 1; k < NX * CPT; ++k) buf[blk_stage<CL, RPT>(c, k)] = float2{0.f, 0.f};
+    }
+    __syncthreads();
+    // copy-out: block x's run of RPT * CPT values goes to item z, rows i0..
+    const int l0 = 1 << l0_log2;
+    const long long z = row0 >> l0_log2;
+    const int i0 = (int)(row0 & (l0 - 1));
+    const int rows_live = nrows - row0 < RPT ? (int)(nrows - row0) : RPT;
+    constexpr int PPR = CPT / 2;              // 16-byte pieces per row of a run
+    constexpr int PIECES = NX * RPT * PPR;
+    float4* hz = reinterpret_cast<float4*>(H + z * os + (long long)i0 * CPT);
+    const float4* st = reinterpret_cast<const float4*>(buf);
+    constexpr int PER = (PIECES + blk_threads(LOG2N) - 1) / blk_threads(LOG2N);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int p = threadIdx.x + u * blk_threads(LOG2N);
+        if (p < PIECES) {
+            const int x = p / (RPT * PPR);
+            const int rem = p - x * (RPT * PPR);
+            if (rem / PPR < rows_live) hz[(long long)x * (l0 * PPR) + rem] = st[p];
+        }
+    }
+}
+
+// C2R: blocked half spectra -> real rows (Z'[k] = (Y[k] + conj Y[n-k]) + i
+// conj(W^k) (Y[k] - conj Y[n-k]), inverse FFT). Non-finite output sets bit 0
+// of *status.
+template <int LOG2N, int CL>
+__global__ void __launch_bounds__(blk_threads(LOG2N), 1024 / blk_threads(LOG2N))
+k_rows_c2r_blk(const float2* __restrict__ H, float2* __restrict__ grid, int l0_log2, long long os,
+               int nrows, const float2* __restrict__ tw, int twn_log2, int* status) {
+    constexpr int n = 1 << LOG2N, q = n >> 4;
+    constexpr int RPT = blk_rows(LOG2N), CPT = 1 << CL, NX = blk_nx(LOG2N, CL);
+    constexpr int SS = blk_seq_stride(LOG2N);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2* buf = reinterpret_cast<float2*>(smraw);
+    const int c = threadIdx.x / q, j = threadIdx.x - c * q;
+    const long long row0 = (long long)blockIdx.x * RPT;
+    const long long row = row0 + c;
+    const bool live = row < nrows;
+    const int l0 = 1 << l0_log2;
+    const long long z = row0 >> l0_log2;
+    const int i0 = (int)(row0 & (l0 - 1));
+    const int rows_live = nrows - row0 < RPT ? (int)(nrows - row0) : RPT;
+    constexpr int PPR = CPT / 2;
+    constexpr int PIECES = NX * RPT * PPR;
+    {
+        // every piece of the CTA in flight at once, then into the staging area
+        const float4* hz = reinterpret_cast<const float4*>(H + z * os + (long long)i0 * CPT);
+        float4* st = reinterpret_cast<float4*>(buf);
+        constexpr int PER = (PIECES + blk_threads(LOG2N) - 1) / blk_threads(LOG2N);
+        float4 t[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int p = threadIdx.x + u * blk_threads(LOG2N);
+            const int x = p / (RPT * PPR);
+            const int rem = p - x * (RPT * PPR);
+            t[u] = p < PIECES && rem / PPR < rows_live ? __ldg(hz + (long long)x * (l0 * PPR) + rem)
+                                                        : float4{0.f, 0.f, 0.f, 0.f};
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int p = threadIdx.x + u * blk_threads(LOG2N);
+            if (p < PIECES) st[p] = t[u];
+        }
+    }
+    __syncthreads();
+    const int sh = twn_log2 - LOG2N - 1;
+    float2 v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int k = j + q * s;
+        const float2 yk = buf[blk_stage<CL, RPT>(c, k)];
+        const float2 ynk = buf[blk_stage<CL, RPT>(c, n - k)];
+        const float2 wk = __ldg(tw + (k << sh));
+        v[s] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
+    }
+    __syncthreads();   // staging read: the buffer becomes the exchange buffer
+    ct_fft<+1, LOG2N, 0, 5>(v, buf + c * SS, j, tw, twn_log2);
+    bool bad = false;
+    if (live) {
+        float2* out = grid + row * n;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            bad |= !(isfinite(v[r].x) && isfinite(v[r].y));
+            out[j + q * r] = v[r];
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+}  // namespace sfft

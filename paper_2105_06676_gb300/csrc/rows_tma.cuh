@@ -48,14 +48,6 @@ __host__ __device__ constexpr size_t row_tma_smem(int log2n) {
     return (size_t)row_tma_rows(log2n) * row_tma_stride(log2n) * 8 + 16;
 }
 
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
-        : "memory");
-}
 
 // DIR = -1: rows of the real grid -> half spectra (R2C); +1: half spectra ->
 // real rows (C2R). src / dst are the grid (complex view of its rows) or H.
