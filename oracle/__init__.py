@@ -21,7 +21,16 @@ Contents
                          Fig. "stencil-fft-algorithm-dD"; closed-form symbol,
                          Appendix "Proof of Eigenvalue-FFT Relation".
 ``recursive_boundary``   StencilFFT-A and RecursiveBoundary in numpy FP64,
-                         Sec. 5 and Fig. "stencil-fft-algorithm-1D-aperiodic".
+                         Sec. 5 and Fig. "stencil-fft-algorithm-1D-aperiodic"
+                         (zero-Dirichlet or reflecting base case).
+``implicit``             implicit stencils Q a_{t+1} = S a_t: dense
+                         pseudoinverse definition and the spectral method with
+                         Lambda_R = Lambda_Q^+ Lambda_S, appendix "Supporting
+                         Implicit Stencils".
+``vector_fields``        vector-valued fields: the plain m-field loop and the
+                         spectral method with a matrix of symbols raised by
+                         repeated squaring, appendix "Supporting Vector Valued
+                         Fields".
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against values the
 paper prints, closed forms, invariants and brute force.
@@ -44,4 +53,17 @@ from .recursive_boundary import (  # noqa: F401
     boundary_distance,
     recursive_boundary,
     stencil_fft_aperiodic,
+)
+from .implicit import (  # noqa: F401
+    implicit_dense,
+    implicit_symbol,
+    stencil_fft_periodic_implicit,
+    stencil_matrix,
+    zero_threshold,
+)
+from .vector_fields import (  # noqa: F401
+    matrix_power_sq,
+    stencil_fft_periodic_vector,
+    symbol_matrix,
+    vector_loop,
 )

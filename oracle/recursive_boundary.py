@@ -2,7 +2,11 @@
 
 Follows Sec. 5 ("Correcting Final Values in the Boundary's Region of
 Influence") and Fig. "stencil-fft-algorithm-1D-aperiodic" in the paper's
-order. The boundary condition is zero Dirichlet: cells outside the grid read 0.
+order. The boundary condition is zero Dirichlet (cells outside the grid read
+0) or reflecting (zero-flux Neumann: the ghost at index -1-k mirrors cell k).
+Sec. 5.1 describes which cells a boundary condition changes, not how: the
+periodic solves keep only cells whose dependence cone never reaches the
+boundary, so the condition enters through the base-case loop alone.
 
 Notation. dist(i) = min over axes of min(i_d + 1, l_d - i_d): the boundary
 lies just outside a[0] and a[l-1] (Sec. 5.2, the 1-D and 2-D region
@@ -23,7 +27,7 @@ Readings taken where the paper is ambiguous:
     the kept cells because their dependence cone (radius sigma T_k) neither
     leaves the region nor crosses the grid boundary.
   * the base case (T < cutoff) evolves the cells with dist <= 2 sigma T by the
-    plain loop with zero ghosts for T steps and keeps dist <= sigma T. The
+    plain loop with the boundary's ghosts for T steps and keeps dist <= sigma T. The
     cutoff must be >= 2 (with cutoff 1, T = 1 would split into T1 = 0,
     T2 = 1 and never terminate).
 """
@@ -51,7 +55,8 @@ def _sigma(weights: np.ndarray) -> int:
 
 
 def recursive_boundary(a: np.ndarray, weights: np.ndarray, T: int,
-                       cutoff: int = 8, dist: np.ndarray | None = None) -> np.ndarray:
+                       cutoff: int = 8, dist: np.ndarray | None = None,
+                       boundary: str = "dirichlet") -> np.ndarray:
     """RecursiveBoundary: from a at dist <= 2 sigma T, the grid at time +T on dist <= sigma T.
 
     Returns a full-shape array; only the cells with dist <= sigma T are
@@ -66,7 +71,7 @@ def recursive_boundary(a: np.ndarray, weights: np.ndarray, T: int,
     # Base case: iterate the loop on the cells within 2 Delta = sigma T.
     if T < cutoff:
         region = np.where(dist <= 2 * sigma * T, a, 0.0)
-        return stencil_loop(region, weights, T, "dirichlet")
+        return stencil_loop(region, weights, T, boundary)
     T1 = T // 2
     T2 = T - T1
     result = np.zeros_like(a)
@@ -77,7 +82,7 @@ def recursive_boundary(a: np.ndarray, weights: np.ndarray, T: int,
     result[keep] = B23[keep]
     # Step 1 (2): recursive call on A1 = a[dist <= 2 sigma T1].
     A1 = np.where(dist <= 2 * sigma * T1, a, 0.0)
-    B1 = recursive_boundary(A1, weights, T1, cutoff, dist)
+    B1 = recursive_boundary(A1, weights, T1, cutoff, dist, boundary)
     keep = dist <= sigma * T1
     result[keep] = B1[keep]
     # B123: time-T1 data on dist <= sigma T + sigma T2.
@@ -89,14 +94,14 @@ def recursive_boundary(a: np.ndarray, weights: np.ndarray, T: int,
     out[keep] = C2[keep]
     # Step 2 (2): recursive call on B12 = B[dist <= 2 sigma T2].
     B12 = np.where(dist <= 2 * sigma * T2, B123, 0.0)
-    C1 = recursive_boundary(B12, weights, T2, cutoff, dist)
+    C1 = recursive_boundary(B12, weights, T2, cutoff, dist, boundary)
     keep = dist <= sigma * T2
     out[keep] = C1[keep]
     return out
 
 
 def stencil_fft_aperiodic(a0: np.ndarray, weights: np.ndarray, T: int,
-                          cutoff: int = 8) -> np.ndarray:
+                          cutoff: int = 8, boundary: str = "dirichlet") -> np.ndarray:
     """StencilFFT-A: interior from StencilFFT-P, boundary region from RecursiveBoundary.
 
     Fig. "stencil-fft-algorithm-1D-aperiodic": result[dist > 2 Delta] comes
@@ -111,6 +116,6 @@ def stencil_fft_aperiodic(a0: np.ndarray, weights: np.ndarray, T: int,
     if interior.any():
         center = stencil_fft_periodic(a0, weights, T)
         result[interior] = center[interior]
-    boundary = recursive_boundary(a0, weights, T, cutoff, dist)
-    result[~interior] = boundary[~interior]
+    near = recursive_boundary(a0, weights, T, cutoff, dist, boundary)
+    result[~interior] = near[~interior]
     return result

@@ -20,6 +20,11 @@
  *     held at 0 supplies the missing neighbours. This is the aperiodic loop of
  *     Fig. "looping-code" with the boundary condition "cells beyond the grid
  *     are zero" (the paper leaves the condition generic).
+ *   - reflecting (zero-flux Neumann) grids (boundary 2) read the mirror image
+ *     across the cell face: index -1-k reads cell k, index l+k reads cell
+ *     l-1-k (half-sample symmetric ghosts, refreshed every step from the
+ *     current values). Sec. 5.1 names Neumann among the aperiodic conditions
+ *     the method covers; the radius must not exceed the axis length.
  *
  * The weights are the stencil coefficients over the box [-r, r]^d in
  * row-major order, entry (m_1 + r, ..., m_d + r). In the paper's
@@ -42,11 +47,18 @@ static int64_t wrap(int64_t i, int64_t n) {
     return q < 0 ? q + n : q;
 }
 
+/* Mirror image of an index at most n cells outside [0, n). */
+static int64_t mirror(int64_t i, int64_t n) {
+    if (i < 0) return -1 - i;
+    if (i >= n) return 2 * n - 1 - i;
+    return i;
+}
+
 /* One step b = S a. Grid shape l0 x l1 x l2 (unused leading axes have
  * length 1 and radius 0). r[k] is the stencil radius along axis k, and the
  * weights are (2r0+1) x (2r1+1) x (2r2+1) row-major. */
 static void one_step(const int64_t l[3], const int r[3], const double* w,
-                     int periodic, const double* a, double* b) {
+                     int boundary, const double* a, double* b) {
     const int64_t n = l[0] * l[1] * l[2];
     const int w1 = 2 * r[1] + 1, w2 = 2 * r[2] + 1;
 #pragma omp parallel for schedule(static)
@@ -59,10 +71,14 @@ static void one_step(const int64_t l[3], const int r[3], const double* w,
             for (int m1 = -r[1]; m1 <= r[1]; ++m1) {
                 for (int m2 = -r[2]; m2 <= r[2]; ++m2) {
                     int64_t j0 = i0 + m0, j1 = i1 + m1, j2 = i2 + m2;
-                    if (periodic) {
+                    if (boundary == 0) {
                         j0 = wrap(j0, l[0]);
                         j1 = wrap(j1, l[1]);
                         j2 = wrap(j2, l[2]);
+                    } else if (boundary == 2) {
+                        j0 = mirror(j0, l[0]);
+                        j1 = mirror(j1, l[1]);
+                        j2 = mirror(j2, l[2]);
                     } else if (j0 < 0 || j0 >= l[0] || j1 < 0 || j1 >= l[1] ||
                                j2 < 0 || j2 >= l[2]) {
                         continue; /* ghost cell: value 0 */
@@ -80,19 +96,20 @@ static void one_step(const int64_t l[3], const int r[3], const double* w,
 /*
  * Evolve a0 by T steps into out (both hold prod(dims) doubles, row-major,
  * last axis contiguous). ndim in 1..3, radius >= 0, boundary 0 = periodic,
- * 1 = zero Dirichlet. nthreads <= 0 keeps the OpenMP default.
+ * 1 = zero Dirichlet, 2 = reflecting (radius <= every axis length).
+ * nthreads <= 0 keeps the OpenMP default.
  * Returns 0 on success, -1 on bad arguments, -2 if scratch allocation fails.
  */
 int oracle_stencil_loop(int ndim, const int64_t* dims, int radius,
                         const double* weights, int boundary, int64_t T,
                         const double* a0, double* out, int nthreads) {
     if (ndim < 1 || ndim > 3 || radius < 0 || T < 0 || !dims || !weights ||
-        !a0 || !out || (boundary != 0 && boundary != 1))
+        !a0 || !out || boundary < 0 || boundary > 2)
         return -1;
     int64_t l[3] = {1, 1, 1};
     int r[3] = {0, 0, 0};
     for (int k = 0; k < ndim; ++k) {
-        if (dims[k] < 1) return -1;
+        if (dims[k] < 1 || (boundary == 2 && radius > dims[k])) return -1;
         l[3 - ndim + k] = dims[k];
         r[3 - ndim + k] = radius;
     }
@@ -111,7 +128,7 @@ int oracle_stencil_loop(int ndim, const int64_t* dims, int radius,
     }
     memcpy(cur, a0, (size_t)n * sizeof(double));
     for (int64_t t = 0; t < T; ++t) {
-        one_step(l, r, weights, boundary == 0, cur, nxt);
+        one_step(l, r, weights, boundary, cur, nxt);
         double* tmp = cur;
         cur = nxt;
         nxt = tmp;

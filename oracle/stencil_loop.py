@@ -70,8 +70,9 @@ def stencil_loop(a0: np.ndarray, weights: np.ndarray, T: int,
     a0       : grid, shape (l_1, ..., l_d), d in 1..3, row-major.
     weights  : stencil coefficients over [-r, r]^d, shape (2r+1,)*d; entry
                (m_1+r, ..., m_d+r) multiplies a_t[i + m].
-    boundary : "periodic" (indices wrap, paper Sec. 1) or "dirichlet" (cells
-               outside the grid read 0).
+    boundary : "periodic" (indices wrap, paper Sec. 1), "dirichlet" (cells
+               outside the grid read 0) or "neumann" (reflecting: index -1-k
+               reads cell k, index l+k reads cell l-1-k).
     """
     a0 = np.ascontiguousarray(a0, dtype=np.float64)
     w = np.ascontiguousarray(weights, dtype=np.float64)
@@ -79,15 +80,16 @@ def stencil_loop(a0: np.ndarray, weights: np.ndarray, T: int,
     if w.ndim != d or len(set(w.shape)) != 1 or w.shape[0] % 2 != 1:
         raise ValueError("weights must have shape (2r+1,)*ndim")
     r = (w.shape[0] - 1) // 2
-    if boundary not in ("periodic", "dirichlet"):
-        raise ValueError("boundary must be 'periodic' or 'dirichlet'")
+    codes = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+    if boundary not in codes:
+        raise ValueError("boundary must be 'periodic', 'dirichlet' or 'neumann'")
     if T < 0:
         raise ValueError("T must be >= 0")
     dims = (ctypes.c_int64 * d)(*a0.shape)
     out = np.empty_like(a0)
     rc = _load().oracle_stencil_loop(
         d, dims, r, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-        0 if boundary == "periodic" else 1, int(T),
+        codes[boundary], int(T),
         a0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nthreads))
     if rc != 0:
