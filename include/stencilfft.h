@@ -61,7 +61,15 @@ extern "C" {
 
 typedef struct stencil_plan_s* stencil_plan_t;
 
-enum stencil_boundary { STENCIL_PERIODIC = 0, STENCIL_ZERO_DIRICHLET = 1 };
+/*
+ * Boundary conditions. STENCIL_NEUMANN is the reflecting (zero-flux) boundary:
+ * the ghost cell at index -1-k reads cell k and the one at l+k reads cell
+ * l-1-k (half-sample mirror, refreshed from the current values every step);
+ * the radius must not exceed any axis length. Both aperiodic conditions use
+ * RecursiveBoundary (paper Sec. 5): its periodic solves keep only cells the
+ * boundary cannot reach, and the condition enters through the base-case loop.
+ */
+enum stencil_boundary { STENCIL_PERIODIC = 0, STENCIL_ZERO_DIRICHLET = 1, STENCIL_NEUMANN = 2 };
 enum stencil_precision {
     STENCIL_FP64 = 0,
     STENCIL_FP32 = 1,
@@ -88,7 +96,7 @@ enum stencil_status_code {
  *   dims      host array of ndim axis lengths, row-major order.
  *   radius    r >= 0 (paper's sigma for box stencils).
  *   weights   host array of (2r+1)^ndim doubles (copied).
- *   boundary  STENCIL_PERIODIC or STENCIL_ZERO_DIRICHLET.
+ *   boundary  STENCIL_PERIODIC, STENCIL_ZERO_DIRICHLET or STENCIL_NEUMANN.
  *   precision STENCIL_FP64, STENCIL_FP32 or STENCIL_FP32_GEMM_*.
  * Allocates the FFT workspace and the twiddle and symbol tables on the
  * current CUDA device and builds them there (twiddles by FP64 sincospi,
@@ -96,6 +104,54 @@ enum stencil_status_code {
  */
 int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
                  const double* weights, int boundary, int precision);
+
+/*
+ * Plan an implicit stencil  Q a_{t+1} = S a_t  on a periodic grid (paper
+ * Sec. 4.2 "Implicit Stencils", appendix "Supporting Implicit Stencils"): the
+ * run advances by the explicit stencil R with symbol
+ * Lambda_R = Lambda_Q^+ Lambda_S, where Lambda_Q^+ is 1 / Lambda_Q where
+ * Lambda_Q is not zero and 0 where it is (|Lambda_Q| <= 2^-40 sum|q| counts as
+ * zero). Where Q is invertible the result satisfies Q a_{t+1} = S a_t.
+ *   weights_s, weights_q  host arrays of (2r+1)^ndim doubles each (copied),
+ *                         in the layout of stencil_plan's weights:
+ *                         (S a)[i] = sum_m weights_s[m] a[i + m], same for Q.
+ *   precision             STENCIL_FP64 or STENCIL_FP32.
+ * Other arguments as for stencil_plan (the boundary is periodic). Every run
+ * multiplies by a table of Lambda_R^T / N built in FP64 on the GPU on the
+ * first run of each T (or by stencil_prepare); stencil_run, stencil_run_host,
+ * stencil_prepare, stencil_symbol_power (which returns Lambda_R^T), status
+ * and destroy apply unchanged. Returns STENCIL_EUNSUPPORTED for other
+ * precisions and for 1-D axes whose packed half length is below 16 or above
+ * what one CTA holds; stencil_plan_set_weights on the plan returns
+ * STENCIL_EUNSUPPORTED.
+ */
+int stencil_plan_implicit(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                          const double* weights_s, const double* weights_q, int precision);
+
+/*
+ * Plan m = nfields coupled scalar fields on a periodic grid (paper Sec. 4.2
+ * "Vector-Valued Fields", appendix "Supporting Vector Valued Fields"):
+ *     a^(i)_{t+1}[x] = sum_j sum_k w_ij[k] a^(j)_t[x + k].
+ * Every field takes the forward Multi-FFT; at every wave vector the m x m
+ * matrix of symbols is raised to the power T by repeated squaring in FP64 on
+ * the GPU (skipped where a bound on its infinity norm shows every entry of the
+ * power below half the smallest subnormal of the pass precision), rounded to
+ * the pass precision and applied to the m spectra; the inverse Multi-FFT
+ * returns every field. This also covers affine stencils (a constant field)
+ * and stencils that read several past steps (one field per step).
+ *   nfields   1..4.
+ *   weights   host array of nfields * nfields * (2r+1)^ndim doubles (copied):
+ *             block (i, j), the stencil taking field j into field i, in the
+ *             layout of stencil_plan's weights.
+ *   precision STENCIL_FP64 or STENCIL_FP32.
+ * Other arguments as for stencil_plan (the boundary is periodic). stencil_run
+ * then takes a device grid of nfields * prod(dims) elements: field i at
+ * offset i * prod(dims). stencil_run_host, stencil_symbol_power and
+ * stencil_plan_set_weights return STENCIL_EUNSUPPORTED for vector plans;
+ * stencil_prepare is a no-op.
+ */
+int stencil_plan_vector(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                        int nfields, const double* weights, int precision);
 
 /*
  * Advance grid by T >= 0 steps in place (paper Fig. "stencil-fft-algorithm-dD"

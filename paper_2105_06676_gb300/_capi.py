@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstencilf
 
 STENCIL_PERIODIC = 0
 STENCIL_ZERO_DIRICHLET = 1
+STENCIL_NEUMANN = 2
 STENCIL_FP64 = 0
 STENCIL_FP32 = 1
 STENCIL_FP32_GEMM_BF16 = 2
@@ -32,6 +33,10 @@ _i64p = _c.POINTER(_c.c_int64)
 _dp = _c.POINTER(_c.c_double)
 SIGNATURES = [
     ("stencil_plan", _c.c_int, [_c.POINTER(_vp), _c.c_int, _i64p, _c.c_int, _dp, _c.c_int, _c.c_int]),
+    ("stencil_plan_implicit", _c.c_int, [_c.POINTER(_vp), _c.c_int, _i64p, _c.c_int, _dp, _dp,
+                                         _c.c_int]),
+    ("stencil_plan_vector", _c.c_int, [_c.POINTER(_vp), _c.c_int, _i64p, _c.c_int, _c.c_int, _dp,
+                                       _c.c_int]),
     ("stencil_run", _c.c_int, [_vp, _vp, _c.c_int64, _vp]),
     ("stencil_run_host", _c.c_int, [_vp, _vp, _vp, _c.c_int64, _vp]),
     ("stencil_symbol_power", _c.c_int, [_vp, _c.c_int64, _vp, _vp]),

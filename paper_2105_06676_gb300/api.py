@@ -13,7 +13,7 @@ import numpy as np
 from . import _capi
 
 _BOUNDARY = {"periodic": _capi.STENCIL_PERIODIC, "dirichlet": _capi.STENCIL_ZERO_DIRICHLET,
-             "zero_dirichlet": _capi.STENCIL_ZERO_DIRICHLET}
+             "zero_dirichlet": _capi.STENCIL_ZERO_DIRICHLET, "neumann": _capi.STENCIL_NEUMANN}
 _PRECISION = {"fp64": _capi.STENCIL_FP64, "fp32": _capi.STENCIL_FP32,
               # FP32 grids with the strided-axis radix-16 DFTs on the tensor cores
               "fp32_gemm_bf16": _capi.STENCIL_FP32_GEMM_BF16,
@@ -41,7 +41,10 @@ def workspace_bytes(dims, radius: int, boundary: str, precision: str) -> int:
 class StencilPlan:
     """A plan for advancing grids of one shape by one stencil (stencil_plan)."""
 
-    def __init__(self, dims, weights, boundary: str = "periodic", precision: str = "fp32"):
+    def __init__(self, dims, weights, boundary: str = "periodic", precision: str = "fp32",
+                 implicit_weights=None):
+        """implicit_weights: Q of an implicit stencil Q a_{t+1} = S a_t (weights
+        then hold S; periodic, fp32 or fp64: stencil_plan_implicit)."""
         w = np.ascontiguousarray(weights, dtype=np.float64)
         dims = tuple(int(x) for x in dims)
         if w.ndim != len(dims) or len(set(w.shape)) != 1 or w.shape[0] % 2 != 1:
@@ -53,10 +56,23 @@ class StencilPlan:
         self.weights = w
         self._handle = ctypes.c_void_p()
         d = (ctypes.c_int64 * len(dims))(*dims)
-        rc = _capi.lib().stencil_plan(ctypes.byref(self._handle), len(dims), d, self.radius,
-                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                      _BOUNDARY[boundary], _PRECISION[precision])
-        _capi.check(rc, "stencil_plan")
+        dp = ctypes.POINTER(ctypes.c_double)
+        if implicit_weights is None:
+            rc = _capi.lib().stencil_plan(ctypes.byref(self._handle), len(dims), d, self.radius,
+                                          w.ctypes.data_as(dp), _BOUNDARY[boundary],
+                                          _PRECISION[precision])
+            _capi.check(rc, "stencil_plan")
+        else:
+            q = np.ascontiguousarray(implicit_weights, dtype=np.float64)
+            if q.shape != w.shape:
+                raise ValueError("implicit_weights must have the shape of weights")
+            if boundary != "periodic":
+                raise ValueError("implicit stencils are periodic")
+            self.implicit_weights = q
+            rc = _capi.lib().stencil_plan_implicit(ctypes.byref(self._handle), len(dims), d,
+                                                   self.radius, w.ctypes.data_as(dp),
+                                                   q.ctypes.data_as(dp), _PRECISION[precision])
+            _capi.check(rc, "stencil_plan_implicit")
 
     @property
     def dtype(self):
@@ -166,6 +182,64 @@ class StencilPlan:
 
     def status(self, stream=None) -> int:
         """Synchronise and return the latched status code (0 or a negative code)."""
+        return int(_capi.lib().stencil_status(self._handle, _stream_ptr(stream)))
+
+    def close(self):
+        if self._handle:
+            _capi.lib().stencil_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class VectorStencilPlan:
+    """m coupled fields on a periodic grid (stencil_plan_vector): weights of
+    shape (m, m, 2r+1, ..., 2r+1), block (i, j) taking field j into field i."""
+
+    def __init__(self, dims, weights, precision: str = "fp32"):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        dims = tuple(int(x) for x in dims)
+        if w.ndim != len(dims) + 2 or w.shape[0] != w.shape[1] or len(set(w.shape[2:])) != 1 \
+                or w.shape[2] % 2 != 1:
+            raise ValueError("weights must have shape (m, m) + (2r+1,)*ndim")
+        self.dims = dims
+        self.nfields = w.shape[0]
+        self.radius = (w.shape[2] - 1) // 2
+        self.precision = precision
+        self.weights = w
+        self._handle = ctypes.c_void_p()
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        rc = _capi.lib().stencil_plan_vector(ctypes.byref(self._handle), len(dims), d, self.radius,
+                                             self.nfields,
+                                             w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             _PRECISION[precision])
+        _capi.check(rc, "stencil_plan_vector")
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def run(self, fields, T: int, stream=None):
+        """Advance a contiguous CUDA tensor of shape (m, *dims) in place by T steps (async)."""
+        shape = (self.nfields,) + self.dims
+        if not fields.is_cuda or fields.dtype != self.dtype or tuple(fields.shape) != shape \
+                or not fields.is_contiguous():
+            raise ValueError(f"fields must be a contiguous CUDA {self.dtype} tensor of shape {shape}")
+        rc = _capi.lib().stencil_run(self._handle, ctypes.c_void_p(fields.data_ptr()), int(T),
+                                     _stream_ptr(stream))
+        _capi.check(rc, "stencil_run")
+        return fields
+
+    def status(self, stream=None) -> int:
         return int(_capi.lib().stencil_status(self._handle, _stream_ptr(stream)))
 
     def close(self):

@@ -144,6 +144,7 @@ struct BaseParams {
     int ndim;
     int gdims[3];
     int Tb;
+    int mirror;       // reflecting boundary: ghosts mirror the cells inside (else zero)
     int wout;         // write cells with dist <= wout
     double w[kMaxWeights];
     float wf[kMaxWeights];
@@ -256,6 +257,49 @@ __global__ void k_tile_copy(const R* __restrict__ Y, R* __restrict__ X,
     }
 }
 
+// Reflecting boundary in the zero-ring tile layout: before every step the
+// ring cells that lie outside the grid take the current value of their mirror
+// image (ghost -1-k <- cell k, ghost l+k <- cell l-1-k), axis by axis so that
+// corner ghosts mirror in every axis. `padded` is the tile's extent plus the
+// ring per axis (3 axes, leading unit axes for 1-D / 2-D tiles), `lo_out` /
+// `hi_out` say which sides of the tile touch the grid boundary; the mirror
+// images lie inside the tile (it covers the first / last RAD cells of an axis
+// it touches). Contains CTA barriers: call it from every thread.
+template <typename R, int RAD>
+__device__ __forceinline__ void mirror_ring(R* b, const int* padded, const bool* lo_out,
+                                            const bool* hi_out) {
+    const int px = padded[2], py = padded[1], pz = padded[0];
+    for (int ax = 2; ax >= 0; --ax) {
+        if (!lo_out[ax] && !hi_out[ax]) continue;
+        const int len = padded[ax];
+        // lines along the other two axes: every cell of the padded box whose
+        // coordinate on ax is a ghost of a boundary side
+        const int others = (pz * py * px) / len;
+        for (int e = threadIdx.x; e < others * 2 * RAD; e += blockDim.x) {
+            const int line = e / (2 * RAD), g = e - line * 2 * RAD;
+            const bool low = g < RAD;
+            const int k = low ? g : g - RAD;
+            if (low ? !lo_out[ax] : !hi_out[ax]) continue;
+            const int dst = low ? RAD - 1 - k : len - RAD + k;
+            const int src = low ? RAD + k : len - RAD - 1 - k;
+            int c[3];
+            // split `line` over the two axes other than ax
+            int rest = line;
+            for (int a = 2; a >= 0; --a) {
+                if (a == ax) continue;
+                c[a] = rest % padded[a];
+                rest /= padded[a];
+            }
+            c[ax] = dst;
+            const int di = (c[0] * py + c[1]) * px + c[2];
+            c[ax] = src;
+            const int si = (c[0] * py + c[1]) * px + c[2];
+            b[di] = b[si];
+        }
+        __syncthreads();
+    }
+}
+
 // 2-D base case: the tile (output box plus a halo of RAD*T_b, clipped to the
 // grid) lives in shared memory with a ring of RAD zero cells around it, so the
 // stencil reads need no bounds tests; each thread owns columns of the tile and
@@ -291,7 +335,11 @@ k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
 #pragma unroll
     for (int i = 0; i < W * W; ++i) w[i] = (R)p.w[i];
     __syncthreads();
+    const bool lo_out[3] = {false, iy0 == 0, ix0 == 0}, hi_out[3] = {false, iy1 == L0, ix1 == L1};
+    const int padded[3] = {1, ey + 2 * RAD, pitch};
+    const bool refl = p.mirror && (lo_out[1] || lo_out[2] || hi_out[1] || hi_out[2]);
     for (int step = 1; step <= p.Tb; ++step) {
+        if (refl) mirror_ring<R, RAD>(b0, padded, lo_out, hi_out);
         const int reach = (p.Tb - step) * RAD;
         const int cy0 = max(t.lo[0] - reach, iy0) - iy0, cy1 = min(t.hi[0] + reach, iy1) - iy0;
         const int cx0 = max(t.lo[1] - reach, ix0) - ix0, cx1 = min(t.hi[1] + reach, ix1) - ix0;
@@ -363,7 +411,11 @@ k_base_1d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
 #pragma unroll
     for (int i = 0; i < W; ++i) w[i] = (R)p.w[i];
     __syncthreads();
+    const bool lo_out[3] = {false, false, i0 == 0}, hi_out[3] = {false, false, i1 == L};
+    const int padded[3] = {1, 1, cells};
+    const bool refl = p.mirror && (lo_out[2] || hi_out[2]);
     for (int step = 1; step <= p.Tb; ++step) {
+        if (refl) mirror_ring<R, RAD>(b0, padded, lo_out, hi_out);
         const int reach = (p.Tb - step) * RAD;
         const int c0 = max(t.lo[0] - reach, i0) - i0, c1 = min(t.hi[0] + reach, i1) - i0;
         for (int x = c0 + threadIdx.x; x < c1; x += blockDim.x) {
@@ -413,7 +465,17 @@ k_base_3d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
                 X[((long long)(lo[0] + z) * L1 + lo[1] + y) * L2 + lo[2] + x];
     }
     __syncthreads();
+    bool lo_out[3], hi_out[3];
+    bool any_out = false;
+    for (int a = 0; a < 3; ++a) {
+        lo_out[a] = lo[a] == 0;
+        hi_out[a] = hi[a] == p.gdims[a];
+        any_out |= lo_out[a] || hi_out[a];
+    }
+    const int padded[3] = {ext[0] + 2 * RAD, py, px};
+    const bool refl = p.mirror && any_out;
     for (int step = 1; step <= p.Tb; ++step) {
+        if (refl) mirror_ring<R, RAD>(b0, padded, lo_out, hi_out);
         const int reach = (p.Tb - step) * RAD;
         int c0[3], c1[3];
         for (int a = 0; a < 3; ++a) {
@@ -1193,6 +1255,7 @@ static cudaError_t launch_base(stencil_plan_s* p, const BaseSet& bs, R* X, R* Y,
     bp.ndim = p->ndim;
     for (int a = 0; a < p->ndim; ++a) bp.gdims[a] = (int)p->dims[a];
     bp.Tb = (int)Tb;
+    bp.mirror = p->boundary == STENCIL_NEUMANN ? 1 : 0;
     bp.wout = whole ? 0x3fffffff : (int)(p->radius * Tb);
     for (int i = 0; i < p->nweights; ++i) {
         bp.w[i] = p->weights[i];
@@ -1425,6 +1488,7 @@ static bool have_device() {
 static ClusterPlan plan_cluster(const stencil_plan_s* p) {
     ClusterPlan cp;
     if (!have_device()) return cp;
+    if (p->boundary == STENCIL_NEUMANN) return cp;   // its ghost planes are zeros
     const int d = p->ndim, r = p->radius;
     const int64_t L0 = p->dims[0];
     const void* kern = p->precision == STENCIL_FP32 ? cluster_kernel_for<float>(r, d)
@@ -1552,7 +1616,7 @@ static double build_loop(const stencil_plan_s* p, Schedule& sc, int64_t T) {
 
 static double build_loop_tiles(const stencil_plan_s* p, Schedule& sc, int64_t T) {
     sc.loop = true;
-    if (p->ndim == 3) {
+    if (p->ndim == 3 && p->boundary != STENCIL_NEUMANN) {   // the step kernels read zero ghosts
         // axis-0 streamed steps: FMA-bound at about 8e12 (FP32) / 3.6e11 (FP64)
         // point updates per second on large grids, about 8 us per step on small
         // ones (GB300 measurements)

@@ -110,6 +110,23 @@ cudaError_t launch_rows_blk(int dir, const void* src, void* dst, int l0_log2, in
 cudaError_t launch_cols_tma_blk(void* H, const ColGeom& g, const void* tw, int twn_log2,
                                 const SymbolSet& ps, int* status, cudaStream_t s);
 
+// Mixed-radix passes (mixed.cu) for transform lengths with prime factors 2, 3,
+// 5, 7 up to 8192: mixed_length_ok says whether a length is covered;
+// launch_mixed_table builds exp(-2 pi i m / len) at pass precision;
+// launch_mixed_rows: dir -1 real rows of 2n values -> half spectra (row
+// stride Mp), +1 back (non-finite output sets bit 0 of *status), twL the table
+// of length 2n; launch_mixed_cols: C2C along a strided axis of length n (tw of
+// length n).
+bool mixed_length_ok(int64_t len, int precision);
+template <typename R>
+cudaError_t launch_mixed_table(void* tw, int len, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mixed_rows(int dir, const void* src, void* dst, long long Mp, int n, int nrows,
+                              const void* twL, int* status, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mixed_cols(int dir, void* H, const ColGeom& g, int n, const void* tw,
+                              cudaStream_t s);
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);
 

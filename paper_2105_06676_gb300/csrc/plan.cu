@@ -122,8 +122,14 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
     for (int a = 0; a < p->ndim; ++a) {
         const int ga = pm[a];
         sp.len[a] = (int)len[a];
-        sp.tshift[a] = ilog2_exact(p->dims[ga]) - ilog2_exact(len[a]);
-        sp.tmask[a] = (int)(len[a] - 1);
+        if (ilog2_exact(len[a]) < 0) {
+            // mixed-radix axis (whole-grid solves only): indices taken modulo l_a
+            sp.tshift[a] = 0;
+            sp.tmask[a] = -1;
+        } else {
+            sp.tshift[a] = ilog2_exact(p->dims[ga]) - ilog2_exact(len[a]);
+            sp.tmask[a] = (int)(len[a] - 1);
+        }
         N *= (double)len[a];
         sp.E64[a] = E64[ga];
         sp.E32[a] = E32[ga];
@@ -147,6 +153,14 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
     }
     sp.scale = 1.0 / N;
     sp.real_symbol = p->real_symbol ? 1 : 0;
+    if (p->implicit) {
+        // the implicit path is periodic only: boxes are the whole grid (no
+        // permutation), so Q's weights keep the plan's order
+        double qsum = 0.0;
+        for (int i = 0; i < p->nweights; ++i) qsum += std::fabs(p->weights_q[i]);
+        sp.wq = p->wq_dev;
+        sp.qzero = qsum * std::ldexp(1.0, -40);
+    }
     // |Lambda - Lambda_fp32| <= sum|w| * 2^-16: a generous bound on the error of
     // at most 343 products of <= 3 rounded table entries and a rounded weight.
     sp.delta = (float)(wsum * std::ldexp(1.0, -16)) + 1e-30f;
@@ -163,7 +177,8 @@ SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int
 static cudaError_t alloc_tables(stencil_plan_s* p) {
     cudaError_t err;
     int64_t tmax = 4;
-    for (int a = 0; a < p->ndim; ++a) tmax = std::max(tmax, p->dims[a]);
+    for (int a = 0; a < p->ndim; ++a)
+        if (ilog2_exact(p->dims[a]) >= 0) tmax = std::max(tmax, p->dims[a]);
     p->twn_log2 = ilog2_exact(tmax);
     const size_t celem = p->precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
     err = cudaMalloc(&p->tw, celem << p->twn_log2);
@@ -181,6 +196,16 @@ static cudaError_t alloc_tables(stencil_plan_s* p) {
         if (err != cudaSuccess) return err;
         err = launch_axis_table(p->E64[a], p->E32[a], (int)p->dims[a], ts);
         if (err != cudaSuccess) return err;
+        if (ilog2_exact(p->dims[a]) < 0) {
+            // mixed-radix axis: its own twiddle table exp(-2 pi i m / l_a)
+            p->mixed = true;
+            err = cudaMalloc(&p->mtw[a], celem * p->dims[a]);
+            if (err != cudaSuccess) return err;
+            p->dev_bytes += celem * p->dims[a];
+            err = p->precision == STENCIL_FP32 ? launch_mixed_table<float>(p->mtw[a], (int)p->dims[a], ts)
+                                               : launch_mixed_table<double>(p->mtw[a], (int)p->dims[a], ts);
+            if (err != cudaSuccess) return err;
+        }
     }
     err = cudaMalloc(&p->status, sizeof(int));
     if (err != cudaSuccess) return err;
@@ -256,7 +281,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         // n1 x n2 passes when one CTA cannot hold the row, and for a single FP64
         // row of >= 512 points: one CTA would leave every other SM's FP64 units
         // idle (4096-point FP64 heat solve 0.155 ms in one CTA)
-        const bool spread = items == 1 && sizeof(R) == 8 && n_log2 >= 9 && !vitems;
+        const bool spread = items == 1 && sizeof(R) == 8 && n_log2 >= 9 && !vitems && !p->implicit;
         if (n > 16 * (sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64) || spread) {
             // n = n1 x n2 passes; Lambda^T per element
             if (vitems) return cudaErrorInvalidValue;
@@ -430,6 +455,9 @@ static void free_plan(stencil_plan_s* p) {
     cudaFree(p->status);
     cudaFree(p->dev_grid);
     cudaFree(p->vt);
+    cudaFree(p->wq_dev);
+    cudaFree(p->wv_dev);
+    for (int a = 0; a < 3; ++a) cudaFree(p->mtw[a]);
     aperiodic_release(p);
     delete p;
 }
@@ -467,11 +495,21 @@ int64_t stencil_max_axis(int ndim, int precision, int axis) {
 
 static int validate(int ndim, const int64_t* dims, int radius, int boundary, int precision) {
     if (ndim < 1 || ndim > 3 || !dims || radius < 0 || radius > kMaxRadius) return STENCIL_EINVAL;
-    if (boundary != STENCIL_PERIODIC && boundary != STENCIL_ZERO_DIRICHLET) return STENCIL_EINVAL;
+    if (boundary != STENCIL_PERIODIC && boundary != STENCIL_ZERO_DIRICHLET &&
+        boundary != STENCIL_NEUMANN)
+        return STENCIL_EINVAL;
     if (precision < STENCIL_FP64 || precision > STENCIL_FP32_GEMM_BF16X3) return STENCIL_EINVAL;
     for (int a = 0; a < ndim; ++a) {
         if (dims[a] < 2 * radius + 1 || dims[a] < 4) return STENCIL_EINVAL;
-        if (ilog2_exact(dims[a]) < 0) return STENCIL_EUNSUPPORTED;
+        if (ilog2_exact(dims[a]) < 0) {
+            // mixed-radix axes: periodic FP32 / FP64 plans, prime factors 2, 3, 5,
+            // 7, an even last axis (real rows of L are n = L/2 complex values)
+            if (boundary != STENCIL_PERIODIC || is_gemm(precision)) return STENCIL_EUNSUPPORTED;
+            const bool last = a == ndim - 1;
+            if (last && (dims[a] % 2)) return STENCIL_EUNSUPPORTED;
+            if (!mixed_length_ok(last ? dims[a] / 2 : dims[a], precision)) return STENCIL_EUNSUPPORTED;
+            continue;
+        }
         if (dims[a] > max_axis(ndim, base_precision(precision), a)) return STENCIL_EUNSUPPORTED;
     }
     if (is_gemm(precision)) {
@@ -487,6 +525,15 @@ size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int bo
                                int precision) {
     if (validate(ndim, dims, radius, boundary, precision) != STENCIL_OK) return 0;
     const int bp = base_precision(precision);
+    bool mixed = false;
+    for (int a = 0; a < ndim; ++a) mixed |= ilog2_exact(dims[a]) < 0;
+    if (mixed) {   // the half spectrum only (1-D: one row), no multiplier table
+        const int64_t n = dims[ndim - 1] / 2;
+        const int64_t align = bp == STENCIL_FP32 ? 16 : 8;
+        int64_t rows = 1;
+        for (int a = 0; a < ndim - 1; ++a) rows *= dims[a];
+        return (size_t)rows * ((n + 1 + align - 1) / align * align) * (bp == STENCIL_FP32 ? 8 : 16);
+    }
     size_t bytes = periodic_workspace_bytes(ndim, dims, bp);
     if (boundary == STENCIL_PERIODIC) bytes += multiplier_table_bytes(ndim, dims, bp);
     return bytes;
@@ -548,12 +595,127 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
             }
         }
     }
+    if (err == cudaSuccess && p->mixed) {
+        // a mixed-radix axis: the plan runs the vector path with one field
+        // (mixed-radix passes around the multiply of vector.cu)
+        if (p->vt) {
+            cudaFree(p->vt);
+            p->vt = nullptr;
+            p->dev_bytes -= multiplier_table_bytes(ndim, dims, precision);
+        }
+        p->vector = true;
+        p->nfields = 1;
+        if (!p->H) {   // 1-D: one row of n + 1 values
+            p->H_bytes = (size_t)p->Mp * 2 * p->elem;
+            err = cudaMalloc(&p->H, p->H_bytes);
+            if (err == cudaSuccess) p->dev_bytes += p->H_bytes;
+        }
+        if (err == cudaSuccess) err = cudaMalloc(&p->wv_dev, p->nweights * sizeof(double));
+        if (err == cudaSuccess) {
+            p->dev_bytes += p->nweights * sizeof(double);
+            err = cudaMemcpy(p->wv_dev, p->weights, p->nweights * sizeof(double),
+                             cudaMemcpyHostToDevice);
+        }
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(cudaStreamPerThread);
     if (err != cudaSuccess) {
         free_plan(p);
         return from_cuda(err);
     }
     *out = p;
+    return STENCIL_OK;
+}
+
+int stencil_plan_implicit(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                          const double* weights_s, const double* weights_q, int precision) {
+    if (!out || !weights_s || !weights_q) return STENCIL_EINVAL;
+    *out = nullptr;
+    int rc = validate(ndim, dims, radius, STENCIL_PERIODIC, precision);
+    if (rc != STENCIL_OK) return rc;
+    if (precision != STENCIL_FP64 && precision != STENCIL_FP32) return STENCIL_EUNSUPPORTED;
+    for (int a = 0; a < ndim; ++a)
+        if (ilog2_exact(dims[a]) < 0) return STENCIL_EUNSUPPORTED;   // power-of-two axes only
+    int nw = 1;
+    for (int a = 0; a < ndim; ++a) nw *= 2 * radius + 1;
+    for (int i = 0; i < nw; ++i)
+        if (!std::isfinite(weights_q[i])) return STENCIL_EINVAL;
+    // every pass must read the multiplier table: a 1-D axis longer than one
+    // CTA holds (its n1 x n2 passes evaluate in-pass) or shorter than 32 points
+    if (multiplier_table_bytes(ndim, dims, precision) == 0 && ndim == 1) return STENCIL_EUNSUPPORTED;
+    rc = stencil_plan(out, ndim, dims, radius, weights_s, STENCIL_PERIODIC, precision);
+    if (rc != STENCIL_OK) return rc;
+    stencil_plan_s* p = *out;
+    p->implicit = true;
+    for (int i = 0; i < nw; ++i) p->weights_q[i] = weights_q[i];
+    p->real_symbol = symmetric_weights(p->weights, ndim, radius) &&
+                     symmetric_weights(p->weights_q, ndim, radius);
+    cudaError_t err = cudaMalloc(&p->wq_dev, nw * sizeof(double));
+    if (err == cudaSuccess) {
+        p->dev_bytes += nw * sizeof(double);
+        err = cudaMemcpy(p->wq_dev, p->weights_q, nw * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (err == cudaSuccess && !p->vt) {
+        // 2-D plans keep no table for explicit stencils: implicit ones need it
+        const size_t vbytes = periodic_workspace_bytes(ndim, dims, precision);
+        err = cudaMalloc(&p->vt, vbytes);
+        if (err == cudaSuccess) p->dev_bytes += vbytes;
+        else p->vt = nullptr;
+    }
+    if (err != cudaSuccess) {
+        free_plan(p);
+        *out = nullptr;
+        return from_cuda(err);
+    }
+    return STENCIL_OK;
+}
+
+int stencil_plan_vector(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
+                        int nfields, const double* weights, int precision) {
+    if (!out || !weights) return STENCIL_EINVAL;
+    *out = nullptr;
+    if (nfields < 1 || nfields > vector_max_fields()) return STENCIL_EINVAL;
+    int rc = validate(ndim, dims, radius, STENCIL_PERIODIC, precision);
+    if (rc != STENCIL_OK) return rc;
+    if (precision != STENCIL_FP64 && precision != STENCIL_FP32) return STENCIL_EUNSUPPORTED;
+    int nw = 1;
+    for (int a = 0; a < ndim; ++a) nw *= 2 * radius + 1;
+    const int total = nfields * nfields * nw;
+    for (int i = 0; i < total; ++i)
+        if (!std::isfinite(weights[i])) return STENCIL_EINVAL;
+    rc = stencil_plan(out, ndim, dims, radius, weights, STENCIL_PERIODIC, precision);
+    if (rc != STENCIL_OK) return rc;
+    stencil_plan_s* p = *out;
+    p->vector = true;
+    p->nfields = nfields;
+    // one half spectrum per field (1-D plans keep none of their own); the
+    // scalar multiplier table is never used
+    cudaFree(p->H);
+    p->dev_bytes -= p->H_bytes;
+    p->H = nullptr;
+    cudaFree(p->vt);
+    p->vt = nullptr;
+    int64_t rows = 1;
+    for (int a = 0; a < ndim - 1; ++a) rows *= dims[a];
+    p->H_bytes = (size_t)nfields * rows * p->Mp * 2 * p->elem;
+    if (p->wv_dev) {   // set up by stencil_plan for a mixed-radix grid
+        cudaFree(p->wv_dev);
+        p->dev_bytes -= p->nweights * sizeof(double);
+        p->wv_dev = nullptr;
+    }
+    cudaError_t err = cudaMalloc(&p->H, p->H_bytes);
+    if (err == cudaSuccess) {
+        p->dev_bytes += p->H_bytes;
+        err = cudaMalloc(&p->wv_dev, total * sizeof(double));
+    }
+    if (err == cudaSuccess) {
+        p->dev_bytes += total * sizeof(double);
+        err = cudaMemcpy(p->wv_dev, weights, total * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (err != cudaSuccess) {
+        free_plan(p);
+        *out = nullptr;
+        return from_cuda(err);
+    }
     return STENCIL_OK;
 }
 
@@ -564,7 +726,8 @@ int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
     if (reinterpret_cast<uintptr_t>(grid) % 16) return STENCIL_EINVAL;
     if (T == 0) return STENCIL_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->boundary == STENCIL_ZERO_DIRICHLET) return aperiodic_run(p, grid, T, s);
+    if (p->boundary != STENCIL_PERIODIC) return aperiodic_run(p, grid, T, s);
+    if (p->vector) return from_cuda(vector_run(p, grid, T, s));
     cudaError_t err;
     const void* vtab = nullptr;
     err = periodic_table(p, T, s, &vtab);
@@ -607,7 +770,7 @@ static cudaError_t periodic_table(stencil_plan_s* p, int64_t T, cudaStream_t s, 
     }
     const bool repeat = p->last_T == T;
     p->last_T = T;
-    if (!repeat) return cudaSuccess;
+    if (!repeat && !p->implicit) return cudaSuccess;   // implicit plans always read the table
     cudaError_t err = build_table(p, T, s);
     if (err != cudaSuccess) return err;
     *out = p->vt;
@@ -629,6 +792,7 @@ static bool mapped_host(const void* a, const void* b, void** da, void** db) {
 int stencil_run_host(stencil_plan_t p, const void* host_in, void* host_out, int64_t T,
                      void* stream) {
     if (!p || !host_in || !host_out || T < 0) return STENCIL_EINVAL;
+    if (p->vector) return STENCIL_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)p->n_cells * p->elem;
     cudaError_t err;
@@ -674,7 +838,7 @@ int stencil_prepare(stencil_plan_t p, int64_t T, void* stream) {
     if (!p || T < 0) return STENCIL_EINVAL;
     if (T == 0) return STENCIL_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->boundary == STENCIL_ZERO_DIRICHLET) return aperiodic_prepare(p, T);
+    if (p->boundary != STENCIL_PERIODIC) return aperiodic_prepare(p, T);
     if (!p->vt || p->vt_T == T) return STENCIL_OK;
     p->last_T = T;
     return from_cuda(build_table(p, T, s));
@@ -682,6 +846,7 @@ int stencil_prepare(stencil_plan_t p, int64_t T, void* stream) {
 
 int stencil_symbol_power(stencil_plan_t p, int64_t T, void* out, void* stream) {
     if (!p || !out || T < 0) return STENCIL_EINVAL;
+    if (p->vector && p->nfields > 1) return STENCIL_EUNSUPPORTED;
     const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
     const int nlast_half = (int)(p->dims[p->ndim - 1] / 2 + 1);
     long long total = nlast_half;
@@ -744,6 +909,7 @@ void plan_set_weights(stencil_plan_s* p, int radius, const double* w) {
 
 extern "C" int stencil_plan_set_weights(stencil_plan_t p, int radius, const double* weights) {
     if (!p || !weights || radius < 0 || radius > kMaxRadius) return STENCIL_EINVAL;
+    if (p->implicit || p->vector) return STENCIL_EUNSUPPORTED;
     int nw = 1;
     for (int a = 0; a < p->ndim; ++a) {
         if (p->dims[a] < 2 * radius + 1) return STENCIL_EINVAL;
@@ -766,7 +932,7 @@ extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
 extern "C" int stencil_plan_autotune(stencil_plan_t p, const void* grid, int64_t T, void* stream,
                                      double* ms, int cap) {
     if (!p || !grid || T < 1 || cap < 0 || (cap > 0 && !ms)) return STENCIL_EINVAL;
-    if (p->boundary != STENCIL_ZERO_DIRICHLET) return STENCIL_EUNSUPPORTED;
+    if (p->boundary == STENCIL_PERIODIC) return STENCIL_EUNSUPPORTED;
     return aperiodic_autotune(p, grid, T, static_cast<cudaStream_t>(stream), ms, cap);
 }
 

@@ -55,6 +55,20 @@ struct stencil_plan_s {
     double weights[sfft::kMaxWeights] = {};
     int nweights = 0;
     bool real_symbol = false;
+    // implicit stencil Q a_{t+1} = S a_t (weights hold S): Q's weights, also
+    // in device memory for the multiplier-table kernel
+    bool implicit = false;
+    double weights_q[sfft::kMaxWeights] = {};
+    double* wq_dev = nullptr;
+    // vector-valued fields (stencil_plan_vector): nfields^2 blocks of
+    // nweights weights in device memory; H holds every field's half spectrum
+    bool vector = false;
+    int nfields = 1;
+    double* wv_dev = nullptr;
+    // mixed-radix axes (length not a power of two): exp(-2 pi i m / l_a) per
+    // such axis at pass precision; such plans run the vector path with one field
+    bool mixed = false;
+    void* mtw[3] = {nullptr, nullptr, nullptr};
     size_t elem = 0;
     int device = 0;
     // twiddles exp(-2 pi i m / 2^twn_log2) at pass precision
@@ -74,6 +88,7 @@ struct stencil_plan_s {
     void* dev_grid = nullptr;
     // Lambda^T / N over the half spectrum of a periodic 3-D or one-CTA 1-D
     // plan, cached for vt_T once a second consecutive run asks for the same T
+    // (implicit plans: every plan shape, built on the first run of each T)
     void* vt = nullptr;
     int64_t vt_T = -1;
     int64_t last_T = -1;
@@ -116,6 +131,11 @@ cudaError_t periodic_solve(stencil_plan_s* p, R* grid, const int64_t* len, int64
 }  // namespace sfft
 
 int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
+namespace sfft {
+// Vector-valued fields (vector.cu): all passes of one run of a vector plan.
+cudaError_t vector_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s);
+int vector_max_fields();
+}  // namespace sfft
 // Builds the schedule, buffers and uploaded tables of T ahead of the first run
 // (allocates; waits for the uploads); returns a status code.
 int aperiodic_prepare(stencil_plan_s* p, int64_t T);

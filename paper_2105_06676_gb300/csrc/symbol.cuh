@@ -39,12 +39,24 @@ struct SymbolParams {
                            // negative when no element can be skipped
     int len[3];            // axis lengths l_a of the solved box (full length of the halved last axis)
     int tshift[3];         // tables hold exp(2 pi i q / (l_a << tshift)): index scale of this box
-    int tmask[3];          // l_a - 1
+    int tmask[3];          // l_a - 1, or -1 for a length that is not a power of two (modulo)
     const double2* E64[3];
     const float2* E32[3];
     double w[kMaxWeights];
     float w32[kMaxWeights];
+    // implicit stencils Q a_{t+1} = S a_t (w holds S): Q's weights in device
+    // memory (null for explicit stencils) and the magnitude at or below which
+    // Lambda_Q counts as zero
+    const double* wq;
+    double qzero;
 };
+
+// Table index of exp(2 pi i (m k mod l_a) / l_a) along axis a.
+__device__ __forceinline__ int axis_index(const SymbolParams& p, int a, int mk) {
+    if (p.tmask[a] >= 0) return (mk & p.tmask[a]) << p.tshift[a];
+    const int v = mk % p.len[a];
+    return v < 0 ? v + p.len[a] : v;
+}
 
 // Symbol parameters for a batch of boxes solved by one launch: up to
 // kMaxOrient orientations (box axes mapped to grid axes by a permutation) and
@@ -168,24 +180,24 @@ struct ColSymbol64 {
 };
 
 template <int RAD>
-__device__ __forceinline__ void col_symbol_init64(const SymbolParams& p, int k1, int k2,
-                                                  ColSymbol64<RAD>& cs) {
+__device__ __forceinline__ void col_symbol_init64(const SymbolParams& p, const double* w, int k1,
+                                                  int k2, ColSymbol64<RAD>& cs) {
     constexpr int W = 2 * RAD + 1;
     if (p.ndim == 1) {
 #pragma unroll
-        for (int i = 0; i < W; ++i) cs.g[i] = double2{p.w[i], 0.0};
+        for (int i = 0; i < W; ++i) cs.g[i] = double2{w[i], 0.0};
         return;
     }
     double2 e1[W];
 #pragma unroll
     for (int m = -RAD; m <= RAD; ++m)
-        e1[m + RAD] = __ldg(p.E64[1] + (((m * k1) & p.tmask[1]) << p.tshift[1]));
+        e1[m + RAD] = __ldg(p.E64[1] + axis_index(p, 1, m * k1));
     if (p.ndim == 2) {
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             double2 inner{0.0, 0.0};
 #pragma unroll
-            for (int jj = 0; jj < W; ++jj) inner = cadd_rn(inner, cscale_rn(e1[jj], p.w[i * W + jj]));
+            for (int jj = 0; jj < W; ++jj) inner = cadd_rn(inner, cscale_rn(e1[jj], w[i * W + jj]));
             cs.g[i] = inner;
         }
         return;
@@ -193,7 +205,7 @@ __device__ __forceinline__ void col_symbol_init64(const SymbolParams& p, int k1,
     double2 e2[W];
 #pragma unroll
     for (int m = -RAD; m <= RAD; ++m)
-        e2[m + RAD] = __ldg(p.E64[2] + (((m * k2) & p.tmask[2]) << p.tshift[2]));
+        e2[m + RAD] = __ldg(p.E64[2] + axis_index(p, 2, m * k2));
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         double2 mid{0.0, 0.0};
@@ -202,7 +214,7 @@ __device__ __forceinline__ void col_symbol_init64(const SymbolParams& p, int k1,
             double2 inner{0.0, 0.0};
 #pragma unroll
             for (int qq = 0; qq < W; ++qq)
-                inner = cadd_rn(inner, cscale_rn(e2[qq], p.w[(i * W + jj) * W + qq]));
+                inner = cadd_rn(inner, cscale_rn(e2[qq], w[(i * W + jj) * W + qq]));
             mid = cadd_rn(mid, cmul_rn(e1[jj], inner));
         }
         cs.g[i] = mid;
@@ -217,7 +229,7 @@ __device__ __forceinline__ double2 col_lambda64(const SymbolParams& p, const Col
 #pragma unroll
     for (int i = 0; i < 2 * RAD + 1; ++i) {
         const int m = i - RAD;
-        const double2 e = __ldg(p.E64[0] + (((m * k0) & p.tmask[0]) << p.tshift[0]));
+        const double2 e = __ldg(p.E64[0] + axis_index(p, 0, m * k0));
         lam = cadd_rn(lam, cmul_rn(e, cs.g[i]));
     }
     return lam;
@@ -229,7 +241,19 @@ __device__ __forceinline__ double2 symbol_pow64(const SymbolParams& p, double2 l
     return cpow_sq(lam, p.T);
 }
 
-// V[k] = Lambda[k]^T / N in FP64 for the column of cs at k_0.
+// Lambda_R = Lambda_Q^+ Lambda_S of an implicit stencil at one frequency
+// (appendix "Supporting Implicit Stencils": the pseudoinverse is 1 / Lambda_Q
+// where Lambda_Q is not zero, 0 where it is).
+__device__ __forceinline__ double2 implicit_ratio(const SymbolParams& p, double2 ls, double2 lq) {
+    const double q2 = __fma_rn(lq.x, lq.x, __dmul_rn(lq.y, lq.y));
+    if (q2 <= __dmul_rn(p.qzero, p.qzero)) return double2{0.0, 0.0};
+    if (p.real_symbol) return double2{__ddiv_rn(ls.x, lq.x), 0.0};
+    // ls conj(lq) / |lq|^2
+    const double2 num = cmul_rn(ls, double2{lq.x, -lq.y});
+    return double2{__ddiv_rn(num.x, q2), __ddiv_rn(num.y, q2)};
+}
+
+// V[k] = Lambda[k]^T / N in FP64 for the column of cs at k_0 (explicit stencils).
 template <int RAD>
 __device__ __forceinline__ double2 col_power64(const SymbolParams& p, const ColSymbol64<RAD>& cs,
                                                int k0) {
@@ -239,11 +263,17 @@ __device__ __forceinline__ double2 col_power64(const SymbolParams& p, const ColS
 template <int RAD>
 __device__ __forceinline__ double2 lambda_pow64_r(const SymbolParams& p, const int* k) {
     ColSymbol64<RAD> cs;
-    col_symbol_init64<RAD>(p, k[1], k[2], cs);
-    return symbol_pow64(p, col_lambda64<RAD>(p, cs, k[0]));
+    col_symbol_init64<RAD>(p, p.w, k[1], k[2], cs);
+    double2 lam = col_lambda64<RAD>(p, cs, k[0]);
+    if (p.wq) {
+        ColSymbol64<RAD> cq;
+        col_symbol_init64<RAD>(p, p.wq, k[1], k[2], cq);
+        lam = implicit_ratio(p, lam, col_lambda64<RAD>(p, cq, k[0]));
+    }
+    return symbol_pow64(p, lam);
 }
 
-// Lambda[k]^T in FP64 (no scale, no shortcut).
+// Lambda[k]^T in FP64 (no scale, no shortcut); Lambda_R^T for implicit stencils.
 static __device__ __noinline__ double2 lambda_pow64(const SymbolParams& p, const int* k) {
     switch (p.r) {
         case 0: return lambda_pow64_r<0>(p, k);
@@ -259,7 +289,7 @@ template <typename C>
 __device__ __forceinline__ C spectral_multiplier(const SymbolParams& p, const int* k) {
     using R = decltype(C{}.x);
     if (p.T == 0) return C{(R)p.scale, (R)0};
-    if (p.use_cut) {
+    if (p.use_cut && !p.wq) {
         const float2 l32 = lambda_eval<float, float2>(p, p.E32, p.w32, k);
         const float bound = hypotf(l32.x, l32.y) + p.delta;
         if (bound < 1.0f) {
@@ -345,7 +375,7 @@ __device__ __noinline__ void multiply_survivors(View sm, int j, int q, unsigned 
                                                 const SymbolParams& p, int k1, int k2) {
     using R = decltype(C{}.x);
     ColSymbol64<RAD> cs;
-    col_symbol_init64<RAD>(p, k1, k2, cs);
+    col_symbol_init64<RAD>(p, p.w, k1, k2, cs);
     while (mask) {
         const int r = __ffs(mask) - 1;
         mask &= mask - 1;

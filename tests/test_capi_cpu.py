@@ -73,11 +73,16 @@ def _plan(lib, dims, radius, boundary=0, precision=1, weights=None):
     ((8, 8, 8, 8), 1, 0, 1, -1),        # ndim 4
     ((16,), -1, 0, 1, -1),              # negative radius
     ((16,), 4, 0, 1, -1),               # radius above the supported maximum
-    ((16,), 1, 2, 1, -1),               # unknown boundary
+    ((16,), 1, 3, 1, -1),               # unknown boundary
     ((16,), 1, 0, 7, -1),               # unknown precision
     ((2,), 0, 0, 1, -1),                # axis shorter than 4
     ((4,), 2, 0, 1, -1),                # axis shorter than 2r+1
-    ((12,), 1, 0, 1, -7),               # not a power of two
+    ((22,), 1, 0, 1, -7),               # a prime factor above 7 (n = 11)
+    ((15,), 1, 0, 1, -7),               # odd last axis (real rows pack pairs)
+    ((12,), 1, 1, 1, -7),               # mixed radix: periodic plans only
+    ((12,), 1, 2, 1, -7),
+    ((96, 64), 1, 0, 2, -7),            # mixed radix: no tensor-core DFTs
+    ((8, 2 * 9 * 1024), 1, 0, 1, -7),   # mixed-radix rows above 8192 complex values
     ((1 << 25,), 1, 0, 1, -7),          # beyond the 1-D limit of 2^24
     ((8, 1 << 16), 1, 0, 1, -7),        # beyond the single-CTA row limit
 ])
@@ -90,6 +95,32 @@ def test_plan_rejects_bad_arguments(lib, dims, radius, boundary, precision, code
     else:
         rc, h = _plan(lib, dims, radius, boundary, precision)
     assert rc == code
+    assert not h.value
+
+
+def test_implicit_and_vector_plans_reject_bad_arguments(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    w = np.full(9, 0.1)
+    h = ctypes.c_void_p()
+    d2 = (ctypes.c_int64 * 2)(64, 64)
+    # implicit: null weights, tensor-core precision, a mixed-radix axis
+    assert lib.stencil_plan_implicit(ctypes.byref(h), 2, d2, 1, w.ctypes.data_as(dp), None, 1) == -1
+    assert lib.stencil_plan_implicit(ctypes.byref(h), 2, (ctypes.c_int64 * 2)(256, 256), 1,
+                                     w.ctypes.data_as(dp), w.ctypes.data_as(dp), 2) == -7
+    assert lib.stencil_plan_implicit(ctypes.byref(h), 2, (ctypes.c_int64 * 2)(60, 64), 1,
+                                     w.ctypes.data_as(dp), w.ctypes.data_as(dp), 1) == -7
+    long1d = (ctypes.c_int64 * 1)(1 << 20)   # n1 x n2 passes take no multiplier table
+    w1 = np.full(3, 0.3)
+    assert lib.stencil_plan_implicit(ctypes.byref(h), 1, long1d, 1, w1.ctypes.data_as(dp),
+                                     w1.ctypes.data_as(dp), 1) == -7
+    # vector: 0 or 5 fields, a tensor-core precision, non-finite weights
+    wv = np.full(4 * 9, 0.1)
+    assert lib.stencil_plan_vector(ctypes.byref(h), 2, d2, 1, 0, wv.ctypes.data_as(dp), 1) == -1
+    assert lib.stencil_plan_vector(ctypes.byref(h), 2, d2, 1, 5, wv.ctypes.data_as(dp), 1) == -1
+    assert lib.stencil_plan_vector(ctypes.byref(h), 2, (ctypes.c_int64 * 2)(256, 256), 1, 2,
+                                   wv.ctypes.data_as(dp), 3) == -7
+    wv[20] = np.inf
+    assert lib.stencil_plan_vector(ctypes.byref(h), 2, d2, 1, 2, wv.ctypes.data_as(dp), 1) == -1
     assert not h.value
 
 
