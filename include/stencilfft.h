@@ -376,6 +376,50 @@ typedef struct {
                             alive and untouched until the ticket completes */
 } stencil_request;
 
+/* ------------------------------------------------------------------------
+ * Batched small periodic solves of mixed shapes (row C1 of the design: the
+ * paper runs independent solves "in parallel", Sec. 5.2, and the Multi-FFT
+ * runs one transform per axis with every other index in parallel, Sec. 4).
+ * An executor keeps a device work list of request descriptors; one run
+ * launches ONE persistent kernel in which every CTA takes the next request
+ * from a device counter and performs its whole StencilFFT-P (R2C rows, the
+ * strided FFTs, the multiply by Lambda^T / N with the FP64 power, the inverse
+ * passes) in shared memory, in place on the request's grid. Requests of one
+ * run may differ in dimension, shape, radius, weights and T.
+ * ------------------------------------------------------------------------ */
+typedef struct stencil_batch_s* stencil_batch_t;
+
+/* Shared memory one request of this shape needs in the executor (bytes), or 0
+ * when the executor does not take it: power-of-two axes of 4..8192, rows *
+ * (n + 1) <= 8192 half-spectrum values (n = half the last axis), at most
+ * 200 KB. precision STENCIL_FP32 or STENCIL_FP64. */
+size_t stencil_batch_smem_bytes(int ndim, const int64_t* dims, int precision);
+
+/* Create an executor for up to `capacity` requests per run (1..2^20) of one
+ * precision (STENCIL_FP32 or STENCIL_FP64) on the current device: twiddle and
+ * symbol tables for axes up to 8192, the device work list, pinned staging.
+ * Returns STENCIL_OK, STENCIL_EINVAL, STENCIL_ENOMEM or STENCIL_ECUDA. */
+int stencil_batch_create(stencil_batch_t* out, int capacity, int precision);
+
+/* Solve `count` requests (host array; boundary STENCIL_PERIODIC, the
+ * executor's precision, stencil_batch_smem_bytes > 0, grids 16-byte aligned
+ * device pointers advanced in place) on `stream`. Uploads the work list and the
+ * requests' symbol parameters, resets the device counter and launches the
+ * persistent kernel; returns before the GPU finishes. A run waits on the host
+ * until the previous run's upload has been read; runs of one executor on
+ * different streams must not overlap (use one executor per stream).
+ * Returns STENCIL_EINVAL / STENCIL_EUNSUPPORTED before any work for a bad
+ * request, STENCIL_ECUDA on a launch failure. */
+int stencil_batch_run(stencil_batch_t b, int count, const stencil_request* reqs, void* stream);
+
+/* Synchronise `stream` and return STENCIL_ENONFINITE if a result since the last
+ * call held a non-finite value (the flag is then cleared), else STENCIL_OK. */
+int stencil_batch_status(stencil_batch_t b, void* stream);
+
+/* Wait for the executor's last run (its completion event, no device-wide
+ * synchronisation) and free it. */
+int stencil_batch_destroy(stencil_batch_t b);
+
 typedef struct {
     uint64_t submitted, completed, failed;
     int max_in_flight;           /* most slots busy at once */

@@ -5,13 +5,13 @@ ABI, include/stencilfft.h); this package is its thin Python binding.
 """
 from . import workloads  # noqa: F401  (seeded inputs; no arithmetic of the method)
 
-__all__ = ["StencilPlan", "VectorStencilPlan", "StencilServer", "solve", "max_axis", "workspace_bytes", "StencilError",
+__all__ = ["StencilPlan", "VectorStencilPlan", "BatchExecutor", "StencilServer", "solve", "max_axis", "workspace_bytes", "StencilError",
            "workloads"]
 
 
 def __getattr__(name):
-    if name in ("StencilPlan", "VectorStencilPlan", "StencilServer", "solve", "max_axis",
-                "workspace_bytes"):
+    if name in ("StencilPlan", "VectorStencilPlan", "BatchExecutor", "StencilServer", "solve",
+                "max_axis", "workspace_bytes"):
         from . import api
         return getattr(api, name)
     if name == "StencilError":

@@ -82,6 +82,11 @@ SIGNATURES += [
     ("stencil_server_wait", _c.c_int, [_vp, _c.c_uint64, _c.c_double, _c.POINTER(_c.c_double)]),
     ("stencil_server_stats", _c.c_int, [_vp, _c.POINTER(ServerStats)]),
     ("stencil_server_destroy", _c.c_int, [_vp]),
+    ("stencil_batch_smem_bytes", _c.c_size_t, [_c.c_int, _i64p, _c.c_int]),
+    ("stencil_batch_create", _c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int]),
+    ("stencil_batch_run", _c.c_int, [_vp, _c.c_int, _c.POINTER(StencilRequest), _vp]),
+    ("stencil_batch_status", _c.c_int, [_vp, _vp]),
+    ("stencil_batch_destroy", _c.c_int, [_vp]),
 ]
 
 _lock = threading.Lock()

@@ -267,6 +267,60 @@ def solve(grid, weights, T: int, boundary: str = "periodic", stream=None):
     return grid
 
 
+class BatchExecutor:
+    """Small periodic solves of mixed shapes in one persistent launch
+    (stencil_batch_*): every request a CUDA tensor solved in place with its own
+    weights and T."""
+
+    def __init__(self, capacity: int, precision: str = "fp32"):
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        _capi.check(_capi.lib().stencil_batch_create(ctypes.byref(self._h), int(capacity),
+                                                     _PRECISION[precision]),
+                    "stencil_batch_create")
+
+    @staticmethod
+    def smem_bytes(dims, precision: str = "fp32") -> int:
+        d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+        return int(_capi.lib().stencil_batch_smem_bytes(len(dims), d, _PRECISION[precision]))
+
+    def run(self, grids, weights, Ts, stream=None):
+        """Enqueue one batch: grids (CUDA tensors), weights and T per request."""
+        n = len(grids)
+        reqs = (_capi.StencilRequest * n)()
+        keep = []
+        for i, (g, w, T) in enumerate(zip(grids, weights, Ts)):
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            keep.append(w)
+            r = reqs[i]
+            r.ndim = g.dim()
+            for a in range(g.dim()):
+                r.dims[a] = int(g.shape[a])
+            r.radius = (w.shape[0] - 1) // 2
+            r.weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            r.boundary = _capi.STENCIL_PERIODIC
+            r.precision = _capi.STENCIL_FP32 if str(g.dtype) == "torch.float32" else _capi.STENCIL_FP64
+            r.T = int(T)
+            r.grid = ctypes.c_void_p(g.data_ptr())
+        rc = _capi.lib().stencil_batch_run(self._h, n, reqs, _stream_ptr(stream))
+        _capi.check(rc, "stencil_batch_run")
+        return grids
+
+    def status(self, stream=None) -> int:
+        return int(_capi.lib().stencil_batch_status(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if self._h:
+            _capi.lib().stencil_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class StencilServer:
     """Continuous-batching request server (stencil_server_*).
 

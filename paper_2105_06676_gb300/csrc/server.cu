@@ -10,11 +10,13 @@
 // its weights on the plan it gets. Requests admitted while others run overlap
 // on the device through their slots' streams.
 //
-// Small periodic requests of one shape are batched: up to kMaxItems queued
-// requests are stacked into one buffer and solved by one launch per pass, each
-// with its own Lambda^T / N table (built from its weights and T), then copied
-// back. A request's result is the same alone or in a batch: the table holds the
-// same FP64-evaluated multipliers the single solve computes.
+// Small periodic requests that one CTA can solve in shared memory are batched
+// across shapes: every queued such request of the head's precision (up to
+// kListCap) goes into one run of a batch executor (stencil_batch_*), one
+// persistent launch over a device work list in which each CTA solves whole
+// requests. Larger small periodic requests of one shape are stacked: up to
+// kMaxItems queued requests share one buffer and one launch per pass, each
+// with its own Lambda^T / N table (built from its weights and T).
 //
 // Latency is measured from submit to the worker observing the request's
 // completion event.
@@ -46,6 +48,7 @@ using namespace sfft;
 namespace {
 
 constexpr int64_t kBatchMaxCells = 1 << 16;   // periodic requests at most this big are batched
+constexpr int kListCap = 256;                  // requests per run of the batch executor
 
 double now_s() {
     using namespace std::chrono;
@@ -80,6 +83,7 @@ struct PlanEntry {
     void* stackH = nullptr;
     void* vt[kMaxItems] = {};
     size_t cells = 0, h_item = 0, v_item = 0;
+    stencil_batch_t exec = nullptr;   // batch key 2: the mixed-shape executor
     cudaEvent_t last = nullptr;   // recorded after the plan's latest launch
 };
 
@@ -124,6 +128,21 @@ bool batchable(const stencil_request& r) {
            r.dims[r.ndim - 1] >= 32 && (r.ndim != 1 || r.dims[0] <= one_cta);
 }
 
+// Solved whole by one CTA of the batch executor, whatever its shape.
+bool list_batchable(const stencil_request& r) {
+    return r.boundary == STENCIL_PERIODIC && stencil_batch_smem_bytes(r.ndim, r.dims, r.precision) > 0;
+}
+
+Key list_key(int precision) {
+    Key k;
+    std::memset(&k, 0, sizeof(k));
+    k.precision = precision;
+    k.boundary = STENCIL_PERIODIC;
+    k.batch = 2;
+    k.radius = -1;
+    return k;
+}
+
 Key key_of(const stencil_request& r, bool batch) {
     Key k;
     std::memset(&k, 0, sizeof(k));
@@ -137,6 +156,8 @@ Key key_of(const stencil_request& r, bool batch) {
 }
 
 size_t estimate_bytes(const Key& k) {
+    if (k.batch == 2)   // executor tables for 8192-point axes, work list, parameters
+        return 8192 * (16 + 8 + 16) + (size_t)kListCap * (sizeof(SymbolParams) + 64);
     const size_t elem = k.precision == STENCIL_FP32 ? 4 : 8;
     int64_t cells = 1;
     for (int a = 0; a < k.ndim; ++a) cells *= k.dims[a];
@@ -191,6 +212,7 @@ void stencil_server_s::release_plan(PlanEntry* pe) {
         cudaEventDestroy(pe->last);
     }
     if (pe->plan) plan_free_idle(pe->plan);
+    if (pe->exec) stencil_batch_destroy(pe->exec);
     cudaFree(pe->stackS);
     cudaFree(pe->stackH);
     for (void* v : pe->vt) cudaFree(v);
@@ -221,6 +243,20 @@ PlanEntry* stencil_server_s::acquire(const Key& k, int* status) {
     }
     PlanEntry* pe = new PlanEntry();
     pe->key = k;
+    if (k.batch == 2) {
+        int rc = stencil_batch_create(&pe->exec, kListCap, k.precision);
+        if (rc == STENCIL_OK && cudaEventCreateWithFlags(&pe->last, cudaEventDisableTiming) != cudaSuccess)
+            rc = STENCIL_ECUDA;
+        if (rc != STENCIL_OK) {
+            *status = rc;
+            release_plan(pe);
+            return nullptr;
+        }
+        pe->bytes = need;
+        in_use += need;
+        plans.push_back(pe);
+        return pe;
+    }
     double w0[kMaxWeights];
     std::fill(w0, w0 + kMaxWeights, 0.0);
     const int r = k.batch ? 0 : k.radius;
@@ -258,6 +294,17 @@ PlanEntry* stencil_server_s::acquire(const Key& k, int* status) {
 // Enqueue the slot's request(s) on its stream; returns a status for them.
 int stencil_server_s::launch(Slot& sl) {
     PlanEntry* pe = sl.pe;
+    if (pe->key.batch == 2) {
+        // mixed shapes: one run of the batch executor, in place on every grid
+        std::vector<stencil_request> reqs(sl.reqs.size());
+        for (size_t i = 0; i < sl.reqs.size(); ++i) {
+            reqs[i] = sl.reqs[i].r;
+            reqs[i].weights = sl.reqs[i].w.data();
+        }
+        const int rc = stencil_batch_run(pe->exec, (int)reqs.size(), reqs.data(), sl.stream);
+        if (rc == STENCIL_OK) sl.batched = (int)reqs.size();
+        return rc;
+    }
     stencil_plan_s* p = pe->plan;
     if (!pe->key.batch) {
         const Pending& q = sl.reqs[0];
@@ -353,8 +400,9 @@ bool stencil_server_s::admit_one(std::unique_lock<std::mutex>& lock) {
         }
     if (!sl) return false;
     const stencil_request head = pending.front().r;
-    const bool batch = batchable(head);
-    const Key k = key_of(head, batch);
+    const bool list = list_batchable(head);
+    const bool batch = !list && batchable(head);
+    const Key k = list ? list_key(head.precision) : key_of(head, batch);
     int status = STENCIL_OK;
     // plan pool work (eviction, creation) without the lock; the head stays at
     // the front meanwhile (only this thread removes requests)
@@ -376,7 +424,18 @@ bool stencil_server_s::admit_one(std::unique_lock<std::mutex>& lock) {
     sl->reqs.clear();
     sl->reqs.push_back(pending.front());
     pending.pop_front();
-    if (batch) {
+    if (list) {
+        // continuous batching across shapes: every queued request one CTA can
+        // solve (same precision) joins this run of the executor
+        for (auto it = pending.begin(); it != pending.end() && (int)sl->reqs.size() < kListCap;) {
+            if (it->r.precision == head.precision && list_batchable(it->r)) {
+                sl->reqs.push_back(*it);
+                it = pending.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    } else if (batch) {
         // continuous batching: pull queued requests of the same shape into this launch
         for (auto it = pending.begin(); it != pending.end() && (int)sl->reqs.size() < kMaxItems;) {
             if (batchable(it->r) && key_of(it->r, true) == k) {
