@@ -418,6 +418,157 @@ def pass_roofline(prof, algo_bytes, peak):
     return out
 
 
+def _cos_modes(dims, ks, amps, base=0.5):
+    """base + sum c cos(2 pi k.x / l): a grid whose periodic evolution under a
+    symmetric star stencil has a closed form (oracle-free check at full size)."""
+    import numpy as np
+    a = np.full(dims, base)
+    axes = np.meshgrid(*[np.arange(l) for l in dims], indexing="ij", sparse=True)
+    for k, c in zip(ks, amps):
+        a = a + c * np.cos(sum(2 * np.pi * kk * x / l for kk, x, l in zip(k, axes, dims)))
+    return a
+
+
+def generalization_lines(flush, check, workers, world):
+    """Secondary lines for the paper's generalisations, each timed with CUDA
+    events (L2 flushed between steps) and checked against the oracle:
+    mixed-radix 8000^2 (the paper's seidel2d size, T = 1e5), implicit
+    Crank-Nicolson 4096^2, two coupled fields 2048^2, reflecting boundary
+    2048^2, and the mixed-shape batch executor."""
+    import numpy as np
+    import torch
+    from paper_2105_06676_gb300 import BatchExecutor, StencilPlan, VectorStencilPlan
+    from paper_2105_06676_gb300 import workloads as wl
+    if check:
+        import oracle
+        from oracle import implicit as oimp
+        from oracle import vector_fields as ovf
+    out = {}
+
+    def timed(plan, a0, T, dt=torch.float32, steps=5):
+        pris = torch.tensor(a0, dtype=dt, device="cuda")
+        g = pris.clone()
+        ts = time_solve(plan, g, pris, flush, steps, 3, T)
+        assert plan.status() == 0
+        ms = sorted(ts)[len(ts) // 2]
+        res = g.double().cpu().numpy()
+        del g, pris
+        return ms, res
+
+    # mixed radix at the paper's 2-D size: 8000^2, 5-point star, T = 1e5
+    dims, T = (8000, 8000), 100000
+    w = wl.weights_star(2, 0.6, 0.1)
+    ks, amps = [(1, 1), (3, 2), (20, 7)], [0.3, 0.2, 0.1]
+    a0 = _cos_modes(dims, ks, amps)
+    plan = StencilPlan(dims, w, "periodic", "fp32")
+    ms, res = timed(plan, a0, T)
+    plan.close()
+    lam = lambda k: 0.6 + sum(0.2 * np.cos(2 * np.pi * kk / l) for kk, l in zip(k, dims))
+    want = _cos_modes(dims, ks, [c * lam(k) ** T for k, c in zip(ks, amps)])
+    out["mixed_radix_8000sq"] = {
+        "workload": "star5_2d_periodic_8000x8000_T100000_fp32 (mixed radix 2^6 5^3)",
+        "ms_per_step": ms, "value": world * 64e6 * T / (ms * 1e-3),
+        "err_vs_oracle": err_rel(res, want, a0), "tolerance": 2e-4,
+        "oracle": "closed form of cosine modes (symmetric star symbol)"}
+    del a0, res, want
+
+    # implicit Crank-Nicolson heat, 4096^2, T = 1000
+    d2 = np.zeros((3, 3)); d2[1, 1] = 1.0
+    L2 = np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], dtype=np.float64)
+    S, Q = d2 + 0.5 * 1.5 * L2, d2 - 0.5 * 1.5 * L2
+    dims, T = (4096, 4096), 1000
+    a0 = wl.grid_uniform(dims, 7001)
+    plan = StencilPlan(dims, S, "periodic", "fp32", implicit_weights=Q)
+    ms, res = timed(plan, a0, T)
+    plan.close()
+    out["implicit_cn_4096sq"] = {
+        "workload": "crank_nicolson_2d_periodic_4096x4096_T1000_fp32", "ms_per_step": ms,
+        "value": world * dims[0] * dims[1] * T / (ms * 1e-3),
+        "err_vs_oracle": (err_rel(res, oimp.stencil_fft_periodic_implicit(a0, S, Q, T, workers=workers), a0)
+                          if check else None), "tolerance": 2e-4,
+        "oracle": "FP64 implicit StencilFFT-P (Lambda_Q^+ Lambda_S)"}
+    del a0, res
+
+    # two coupled fields, 2048^2, T = 1000
+    rng = np.random.default_rng(7002)
+    W = rng.random((2, 2, 3, 3))
+    W /= W.sum(axis=(1, 2, 3), keepdims=True)
+    dims, T = (2048, 2048), 1000
+    a0 = np.stack([wl.grid_uniform(dims, 7003), wl.grid_uniform(dims, 7004)])
+    vplan = VectorStencilPlan(dims, W, "fp32")
+    ms, res = timed(vplan, a0, T)
+    vplan.close()
+    out["vector_2fields_2048sq"] = {
+        "workload": "two_fields_2d_periodic_2048x2048_T1000_fp32", "ms_per_step": ms,
+        "value": world * 2 * dims[0] * dims[1] * T / (ms * 1e-3),
+        "err_vs_oracle": (err_rel(res, ovf.stencil_fft_periodic_vector(a0, W, T, workers=workers), a0)
+                          if check else None), "tolerance": 2e-4,
+        "oracle": "FP64 vector StencilFFT-P (matrix of symbols by repeated squaring)"}
+    del a0, res
+
+    # reflecting boundary, 2048^2 symmetric 9-point box, T = 1000
+    wsym = np.array([[0.05, 0.1, 0.05], [0.15, 0.3, 0.15], [0.05, 0.1, 0.05]])
+    dims, T = (2048, 2048), 1000
+    a0 = wl.grid_uniform(dims, 7005)
+    plan = StencilPlan(dims, wsym, "neumann", "fp32")
+    plan.run(torch.tensor(a0, dtype=torch.float32, device="cuda"), T)   # schedule set-up
+    ms, res = timed(plan, a0, T, steps=3)
+    plan.close()
+    err = None
+    if check:
+        ext = np.concatenate([a0, a0[::-1]], axis=0)
+        ext = np.concatenate([ext, ext[:, ::-1]], axis=1)
+        err = err_rel(res, oracle.stencil_fft_periodic(ext, wsym, T, workers=workers)[:dims[0], :dims[1]], a0)
+    out["neumann_2048sq"] = {
+        "workload": "box9_2d_reflecting_2048x2048_T1000_fp32", "ms_per_step": ms,
+        "value": world * dims[0] * dims[1] * T / (ms * 1e-3), "err_vs_oracle": err,
+        "tolerance": 2e-4, "oracle": "FP64 periodic solve of the even extension"}
+    del a0, res
+
+    # batch executor: 512 mixed small periodic requests in one persistent launch
+    shapes = [(4096,), (64, 64), (128, 32), (32, 128), (16, 16, 16), (64, 16), (8, 32, 32)]
+    reqs = []
+    for i in range(512):
+        d = shapes[i % len(shapes)]
+        reqs.append((d, wl.weights_random_box(len(d), 1, 8000 + i), int(10 ** rng.uniform(1, 4)),
+                     wl.grid_uniform(d, 9000 + i)))
+    ex = BatchExecutor(len(reqs), "fp32")
+    pris = [torch.tensor(a, dtype=torch.float32, device="cuda") for (_, _, _, a) in reqs]
+    grids = [p.clone() for p in pris]
+    ws = [w for (_, w, _, _) in reqs]
+    Ts = [T for (_, _, T, _) in reqs]
+    for _ in range(3):
+        ex.run(grids, ws, Ts)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(5):
+        for g, p in zip(grids, pris):
+            g.copy_(p)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ex.run(grids, ws, Ts)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert ex.status() == 0
+    ex.close()
+    ms = sorted(times)[2]
+    upd = sum(int(np.prod(d)) * T for (d, _, T, _) in reqs)
+    errs = []
+    if check:
+        for i in range(0, len(reqs), 37):
+            d, w, T, a = reqs[i]
+            errs.append(err_rel(grids[i].double().cpu().numpy(), oracle.stencil_fft_periodic(a, w, T), a))
+    out["batch_executor_512_mixed"] = {
+        "workload": "512 small periodic requests of 7 shapes (1-D 4096 .. 3-D 16^3), T in [10, 1e4], r = 1, FP32",
+        "ms_per_batch": ms, "requests_per_s": len(reqs) / (ms * 1e-3),
+        "value": world * upd / (ms * 1e-3), "unit": "point-updates/s", "kernel_launches_per_batch": 1,
+        "err_vs_oracle_max": max(errs) if errs else None, "err_vs_oracle_sampled": len(errs),
+        "tolerance": 2e-4}
+    return out
+
+
 # GB300 FP64 FMA rate measured once on this pool with a one-kernel
 # microbenchmark (a grid-stride loop of independent DFMA chains on every SM,
 # CUDA events; no clock or power changes).
@@ -442,6 +593,8 @@ def main():
                     help="run the serving measurement alone and print its JSON (long streams)")
     ap.add_argument("--no-dirichlet", action="store_true",
                     help="skip the zero-Dirichlet secondary measurement (short profiling runs)")
+    ap.add_argument("--no-general", action="store_true",
+                    help="skip the implicit / vector / reflecting / mixed-radix / batch lines")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the FP64 oracle comparisons of the results (short profiling runs)")
     ap.add_argument("--only-headline", action="store_true",
@@ -648,6 +801,9 @@ def main():
             del gs
         del outd
 
+    # ---- the paper's generalisations and the batch executor (secondary)
+    general = generalization_lines(flush, check, workers, world) if not args.no_general else None
+
     # ---- serving: mixed stream through the continuous-batching server
     serving = (serve_mixed_stream(args.serve_requests,
                                   tuple(float(x) for x in args.serve_loads.split(",")),
@@ -722,6 +878,7 @@ def main():
                          # the whole solve (three passes) against the same peak
                          "step_bytes": sum(algo.values()),
                          "step_frac": sum(algo.values()) / (ms32 * 1e-3) / 1e9 / peak},
+            "generalizations": general,
             "serving": serving,
             "gpu_launches": int(round(step_kernel_launches * args.steps)),
             "clocks": clocks,

@@ -276,12 +276,27 @@ int stencil_plan_set_schedule(stencil_plan_t plan, int mode);
  * ms[i] for the first cap of five fixed slots -- 0 recursive, 1 loop,
  * 2 recursive with half the cutoff, 3 recursive with twice the cutoff,
  * 4 cluster-resident loop; -1 for a slot that does not apply -- and returns
- * the slot of the one kept. Synchronises stream. Errors: STENCIL_EINVAL (NULL plan or
- * grid, T < 1, cap < 0, ms NULL with cap > 0), STENCIL_EUNSUPPORTED for
- * periodic plans (one schedule only), the status of a failing run.
+ * the slot of the one kept.
+ * Periodic 2-D / 3-D plans (not implicit, vector, mixed-radix or tensor-core
+ * plans): times the four pass variants -- 0 the default (FP32 2-D: half
+ * spectrum in column blocks, TMA-fed column and C2R passes), 1 row-major half
+ * spectrum with the TMA-fed passes, 2 the register kernels only with
+ * 1024-thread FP32 column CTAs, 3 the register kernels with 512-thread column
+ * CTAs -- four timed runs each after two warm-up runs, keeps the fastest for
+ * this plan and for plans of the same shape and precision created later in
+ * this process; ms[i] holds variant i's mean time.
+ * Synchronises stream. Errors: STENCIL_EINVAL (NULL plan or grid, T < 1,
+ * cap < 0, ms NULL with cap > 0), STENCIL_EUNSUPPORTED for the periodic plans
+ * named above and 1-D periodic plans, the status of a failing run.
  */
 int stencil_plan_autotune(stencil_plan_t plan, const void* grid, int64_t T, void* stream,
                           double* ms, int cap);
+
+/* Set a periodic plan's pass variant (0..3 as listed for stencil_plan_autotune,
+ * -1 for the default selection). Variants change kernels and layouts only, not
+ * the result beyond rounding. STENCIL_EINVAL for other values,
+ * STENCIL_EUNSUPPORTED for aperiodic plans. */
+int stencil_plan_set_pass_variant(stencil_plan_t plan, int variant);
 
 /*
  * Per-kernel timing (measurement support, not part of the paper's method).

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("stencil_plan_set_cutoff", _c.c_int, [_vp, _c.c_int64]),
     ("stencil_plan_set_schedule", _c.c_int, [_vp, _c.c_int]),
     ("stencil_plan_autotune", _c.c_int, [_vp, _vp, _c.c_int64, _vp, _c.POINTER(_c.c_double), _c.c_int]),
+    ("stencil_plan_set_pass_variant", _c.c_int, [_vp, _c.c_int]),
     ("stencil_profile_enable", _c.c_int, [_vp, _c.c_int]),
     ("stencil_profile_read", _c.c_int, [_vp, _c.POINTER(_c.c_double), _i64p, _c.c_int]),
     ("stencil_profile_kind_name", _c.c_char_p, [_c.c_int]),

@@ -101,15 +101,25 @@ class StencilPlan:
                     "stencil_plan_set_cutoff")
 
     def autotune(self, grid, T: int, stream=None) -> dict:
-        """Time the zero-Dirichlet schedules for T on a copy of `grid` (CUDA tensor,
-        unchanged) and keep the fastest (stencil_plan_autotune)."""
-        names = ["recursive", "loop", "recursive_half_cutoff", "recursive_double_cutoff", "cluster"]
+        """Time the zero-Dirichlet schedules, or the periodic pass variants, for T
+        on a copy of `grid` (CUDA tensor, unchanged) and keep the fastest
+        (stencil_plan_autotune)."""
+        if self.boundary == "periodic":
+            names = ["blocked_tma", "rowmajor_tma", "register_1024", "register_512"]
+        else:
+            names = ["recursive", "loop", "recursive_half_cutoff", "recursive_double_cutoff",
+                     "cluster"]
         ms = (ctypes.c_double * len(names))()
         rc = _capi.lib().stencil_plan_autotune(self._handle, ctypes.c_void_p(grid.data_ptr()), int(T),
                                                _stream_ptr(stream), ms, len(names))
         if rc < 0:
             _capi.check(rc, "stencil_plan_autotune")
         return {"chosen": names[rc], "ms": {n: ms[i] for i, n in enumerate(names) if ms[i] >= 0}}
+
+    def set_pass_variant(self, variant: int) -> None:
+        """Periodic pass variant 0..3 (-1: default), stencil_plan_set_pass_variant."""
+        _capi.check(_capi.lib().stencil_plan_set_pass_variant(self._handle, int(variant)),
+                    "stencil_plan_set_pass_variant")
 
     def set_schedule(self, mode: str) -> None:
         """Zero-Dirichlet schedule: "auto", "recursive", "loop" or "cluster"

@@ -127,6 +127,20 @@ template <typename R>
 cudaError_t launch_mixed_cols(int dir, void* H, const ColGeom& g, int n, const void* tw,
                               cudaStream_t s);
 
+// Pass variant of the periodic solve running on this host thread (set by
+// batched_solve from the plan, chosen by stencil_plan_autotune): 0 the default
+// (FP32 2-D: blocked half spectrum; TMA-fed column and C2R passes), 1 the
+// row-major half spectrum with the TMA-fed passes, 2 the register kernels
+// only (1024-thread FP32 column CTAs), 3 the register kernels with 512-thread
+// column CTAs. -1 leaves the selection to the defaults.
+int pass_variant();
+struct PassVariantScope {
+    int saved;
+    explicit PassVariantScope(int v);
+    ~PassVariantScope();
+};
+constexpr int kPassVariants = 4;
+
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device.
 cudaError_t smem_optin(const void* kernel, size_t bytes);
 

@@ -40,6 +40,11 @@ __global__ void k_symbol_table(double2* out, const __grid_constant__ SymbolParam
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
+static thread_local int t_pass_variant = -1;
+int pass_variant() { return t_pass_variant; }
+PassVariantScope::PassVariantScope(int v) : saved(t_pass_variant) { t_pass_variant = v; }
+PassVariantScope::~PassVariantScope() { t_pass_variant = saved; }
+
 cudaError_t smem_optin(const void* kernel, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<const void*, int>, size_t> done;

@@ -56,7 +56,7 @@ bool tma_enabled() {
         const char* e = std::getenv("STENCILFFT_COLS");
         return !(e && std::strcmp(e, "reg") == 0);
     }();
-    return on;
+    return on && pass_variant() < 2;
 }
 
 // 5-D view of the passes' geometry: (floats of a row of columns, mid, 256 rows,
@@ -247,7 +247,7 @@ static bool blocked_enabled() {
         const char* e = std::getenv("STENCILFFT_BLOCKED");
         return !(e && std::strcmp(e, "0") == 0);
     }();
-    return on;
+    return on && pass_variant() < 1;
 }
 
 bool blocked_ok(const void* grid, const void* H, int l0_log2, int n_log2) {

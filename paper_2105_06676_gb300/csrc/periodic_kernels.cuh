@@ -729,7 +729,7 @@ static int col_threads_cap() {
         const int v = e ? std::atoi(e) : 1024;
         return v == 512 ? 512 : 1024;
     }();
-    return cap;
+    return pass_variant() == 3 ? 512 : cap;
 }
 
 // Transform lengths (log2) with compile-time specialised register kernels;

@@ -11,6 +11,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -264,6 +267,7 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
     const int d = p->ndim;
     if (items < 1 || items > kMaxItems || norient < 1 || norient > kMaxOrient)
         return cudaErrorInvalidValue;
+    const PassVariantScope variant(p->pass_variant);
     SymbolSet ss;
     std::memset(&ss, 0, sizeof(ss));
     for (int o = 0; o < norient; ++o)
@@ -539,6 +543,8 @@ size_t stencil_workspace_bytes(int ndim, const int64_t* dims, int radius, int bo
     return bytes;
 }
 
+int tuned_variant(const stencil_plan_s* p);
+
 int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
                  const double* weights, int boundary, int precision) {
     if (!out || !weights) return STENCIL_EINVAL;
@@ -622,6 +628,7 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
         free_plan(p);
         return from_cuda(err);
     }
+    if (boundary == STENCIL_PERIODIC) p->pass_variant = tuned_variant(p);
     *out = p;
     return STENCIL_OK;
 }
@@ -929,10 +936,88 @@ extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     return STENCIL_OK;
 }
 
+// Size classes tuned in this process: (ndim, dims, precision) -> pass variant;
+// new periodic plans of a tuned class start with its choice.
+static std::mutex g_tuned_mu;
+static std::map<std::vector<int64_t>, int> g_tuned;
+
+static std::vector<int64_t> size_class(const stencil_plan_s* p) {
+    return {p->ndim, p->dims[0], p->dims[1], p->dims[2], p->precision, p->gemm};
+}
+
+int tuned_variant(const stencil_plan_s* p) {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    auto it = g_tuned.find(size_class(p));
+    return it == g_tuned.end() ? -1 : it->second;
+}
+
+// Periodic plans: time every pass variant (PassVariantScope) on a scratch copy
+// of grid for T and keep the fastest, for this plan and its size class.
+static int periodic_autotune(stencil_plan_s* p, const void* grid, int64_t T, cudaStream_t s,
+                             double* ms, int cap) {
+    if (p->vector || p->implicit || p->ndim < 2 || p->gemm >= 0) return STENCIL_EUNSUPPORTED;
+    const size_t bytes = (size_t)p->n_cells * p->elem;
+    void* scratch = nullptr;
+    cudaError_t err = cudaMalloc(&scratch, bytes);
+    if (err != cudaSuccess) return from_cuda(err);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int keep = p->pass_variant;
+    int best = -1;
+    double best_ms = 0.0;
+    int rc = STENCIL_OK;
+    for (int v = 0; v < kPassVariants && rc == STENCIL_OK; ++v) {
+        p->pass_variant = v;
+        double t = 0.0;
+        for (int rep = 0; rep < 6 && rc == STENCIL_OK; ++rep) {
+            err = cudaMemcpyAsync(scratch, grid, bytes, cudaMemcpyDeviceToDevice, s);
+            if (err != cudaSuccess) rc = from_cuda(err);
+            if (rc == STENCIL_OK && rep >= 2) cudaEventRecord(e0, s);
+            if (rc == STENCIL_OK) rc = stencil_run(p, scratch, T, s);
+            if (rc == STENCIL_OK && rep >= 2) {
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = STENCIL_ECUDA;
+                float f = 0.f;
+                cudaEventElapsedTime(&f, e0, e1);
+                t += f / 4.0;
+            }
+        }
+        if (rc != STENCIL_OK) break;
+        if (v < cap) ms[v] = t;
+        if (best < 0 || t < best_ms) {
+            best = v;
+            best_ms = t;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (rc != STENCIL_OK) {
+        p->pass_variant = keep;
+        return rc;
+    }
+    p->pass_variant = best;
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mu);
+        g_tuned[size_class(p)] = best;
+    }
+    return best;
+}
+
+extern "C" int stencil_plan_set_pass_variant(stencil_plan_t p, int variant) {
+    if (!p || variant < -1 || variant >= kPassVariants) return STENCIL_EINVAL;
+    if (p->boundary != STENCIL_PERIODIC) return STENCIL_EUNSUPPORTED;
+    p->pass_variant = variant;
+    return STENCIL_OK;
+}
+
 extern "C" int stencil_plan_autotune(stencil_plan_t p, const void* grid, int64_t T, void* stream,
                                      double* ms, int cap) {
     if (!p || !grid || T < 1 || cap < 0 || (cap > 0 && !ms)) return STENCIL_EINVAL;
-    if (p->boundary == STENCIL_PERIODIC) return STENCIL_EUNSUPPORTED;
+    if (p->boundary == STENCIL_PERIODIC)
+        return periodic_autotune(p, grid, T, static_cast<cudaStream_t>(stream), ms, cap);
     return aperiodic_autotune(p, grid, T, static_cast<cudaStream_t>(stream), ms, cap);
 }
 

@@ -99,6 +99,7 @@ struct stencil_plan_s {
     int gemm = -1;       // tensor-core DFT operand mode (kGemm*), -1: CUDA-core FFTs
     Profiler prof;
     bool use_graphs = true;   // replay zero-Dirichlet runs as CUDA graphs
+    int pass_variant = -1;    // periodic pass variant (PassVariantScope); -1 default
     size_t dev_bytes = 0;     // device memory this plan holds
 };
 

@@ -403,3 +403,52 @@ def test_set_weights_reuses_the_plan(boundary):
         ref = oracle.stencil_loop(a0, w, 37, boundary)
         assert err_rel(g.cpu().numpy(), ref, a0) <= TOL["fp64"]
     plan.close()
+
+
+@pytest.mark.parametrize("dims,precision", [((4096, 4096), "fp32"), ((512, 1024), "fp32"),
+                                            ((128, 64, 256), "fp32"), ((1024, 1024), "fp64")])
+def test_periodic_autotune_variants_agree_and_choice_sticks(dims, precision):
+    # every pass variant gives the oracle's result; the fastest is kept by the
+    # plan and by later plans of the same shape
+    from paper_2105_06676_gb300 import StencilPlan
+    T = 333
+    w = wl.weights_random_box(len(dims), 1, 61)
+    a0 = wl.grid_uniform(dims, 62)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan = StencilPlan(dims, w, "periodic", precision)
+    res = plan.autotune(g, T)
+    assert res["chosen"] in res["ms"] and len(res["ms"]) == 4
+    np.testing.assert_array_equal(g.cpu().numpy(), a0.astype(np.float32 if precision == "fp32" else np.float64))
+    plan.run(g, T)
+    assert plan.status() == 0
+    got = g.double().cpu().numpy()
+    plan.close()
+    ref = oracle.stencil_fft_periodic(a0, w, T, workers=8)
+    tol = 1e-10 if precision == "fp64" else 2e-4
+    assert err_rel(got, ref, a0) <= tol
+    plan2 = StencilPlan(dims, w, "periodic", precision)
+    g2 = torch.tensor(a0, dtype=dt, device="cuda")
+    plan2.run(g2, T)
+    plan2.close()
+    np.testing.assert_array_equal(g2.double().cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("dims,precision", [((4096, 2048), "fp32"), ((1024, 512), "fp32"),
+                                            ((64, 128, 256), "fp32"), ((512, 256), "fp64")])
+def test_periodic_pass_variants_match_oracle(variant, dims, precision):
+    from paper_2105_06676_gb300 import StencilPlan
+    T = 77
+    w = wl.weights_random_box(len(dims), 1, 63)
+    a0 = wl.grid_uniform(dims, 64)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = StencilPlan(dims, w, "periodic", precision)
+    plan.set_pass_variant(variant)
+    g = torch.tensor(a0, dtype=dt, device="cuda")
+    plan.run(g, T)
+    assert plan.status() == 0
+    plan.close()
+    ref = oracle.stencil_fft_periodic(a0, w, T, workers=8)
+    tol = 1e-10 if precision == "fp64" else 2e-4
+    assert err_rel(g.double().cpu().numpy(), ref, a0) <= tol
