@@ -260,7 +260,18 @@ k_cols_tma(float2* __restrict__ H, const __grid_constant__ CUtensorMap map,
             const SymbolParams& p = ps.p[ps.orient[z]];
             const float2* vt = static_cast<const float2*>(ps.vtab_item[z] ? ps.vtab_item[z]
                                                                           : ps.vtab[ps.orient[z]]);
-            if (vt) {
+            if (BLK && vt && ps.vflags) {
+                // blocked table: this tile's 64 KB block, or nothing at all when
+                // every multiplier of the block is zero
+                if (__ldg(ps.vflags + x)) {
+                    const float2* vb = vt + (long long)x * kTileElems + c;
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], __ldg(vb + (j + q * r) * CPT));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = float2{0.f, 0.f};
+                }
+            } else if (vt) {
                 // multipliers shared by every solve of this shape and T
                 const float2* vb = vt + (long long)y * g.ms + i0 + c;
                 const long long vs = BLK ? g.vS : g.S;   // tables keep the row-major layout

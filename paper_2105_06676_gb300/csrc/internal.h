@@ -104,6 +104,12 @@ cudaError_t launch_rows_tma(int dir, const void* src, void* dst, long long Mp, i
 // stride of multiplier tables). All return cudaErrorNotSupported when not
 // applicable.
 bool blocked_ok(const void* grid, const void* H, int l0_log2, int n_log2);
+// The blocked path applies to a 2-D shape (dims only; pointers aside), and its
+// repeated-T multiplier table: V = Lambda^T / N laid out like the blocked half
+// spectrum of one item plus one flag per column block (0: all zero).
+bool blocked_shape(int ndim, const int64_t* dims);
+cudaError_t launch_vtable_blk(void* V, int* flags, const SymbolParams& p, int l0_log2, int n_log2,
+                              cudaStream_t s);
 long long blocked_item_elems(int l0_log2, int n_log2);
 cudaError_t launch_rows_blk(int dir, const void* src, void* dst, int l0_log2, int n_log2,
                             int nrows, const void* tw, int twn_log2, int* status, cudaStream_t s);

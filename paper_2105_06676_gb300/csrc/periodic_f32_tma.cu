@@ -250,6 +250,56 @@ static bool blocked_enabled() {
     return on && pass_variant() < 1;
 }
 
+// V = Lambda^T / N in the blocked layout of the half spectrum (one 2-D item)
+// and one flag per column block: set when a multiplier of the block is not 0.
+__global__ void k_vtable_blk(float2* __restrict__ V, int* __restrict__ flags,
+                             const __grid_constant__ SymbolParams p, int l0_log2, int cl, int n,
+                             long long total) {
+    const int l0 = 1 << l0_log2, cpt = 1 << cl;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e >> 13);              // 8192 values per block
+        const int rem = (int)(e & 8191);
+        const int i = rem >> cl, c = rem & (cpt - 1);
+        const int k1 = x * cpt + c;
+        float2 v{0.f, 0.f};
+        if (k1 <= n) {
+            const int k[3] = {i, k1, 0};
+            v = spectral_multiplier<float2>(p, k);
+        }
+        V[e] = v;
+        if (v.x != 0.f || v.y != 0.f) flags[x] = 1;
+    }
+    (void)l0;
+}
+
+static int log2_or_neg(int64_t v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+bool blocked_shape(int ndim, const int64_t* dims) {
+    if (ndim != 2) return false;
+    const int l0 = log2_or_neg(dims[0]), l1 = log2_or_neg(dims[1]);
+    if (l0 < 0 || l1 < 0) return false;
+    return l0 >= kTmaLog2Lo && l0 <= kTmaLog2Hi && l1 - 1 >= kBlkLog2Lo && l1 - 1 <= kBlkLog2Hi;
+}
+
+cudaError_t launch_vtable_blk(void* V, int* flags, const SymbolParams& p, int l0_log2, int n_log2,
+                              cudaStream_t s) {
+    const long long total = blocked_item_elems(l0_log2, n_log2);
+    const int nx = (int)(total >> 13);
+    cudaError_t err = cudaMemsetAsync(flags, 0, nx * sizeof(int), s);
+    if (err != cudaSuccess) return err;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_vtable_blk<<<(int)blocks, 256, 0, s>>>(static_cast<float2*>(V), flags, p, l0_log2,
+                                             tma_cols_log2(l0_log2), 1 << n_log2, total);
+    return cudaGetLastError();
+}
+
 bool blocked_ok(const void* grid, const void* H, int l0_log2, int n_log2) {
     if (!tma_enabled() || !blocked_enabled() || sm_count() <= 0) return false;
     if (l0_log2 < kTmaLog2Lo || l0_log2 > kTmaLog2Hi) return false;

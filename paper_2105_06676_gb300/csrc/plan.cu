@@ -224,6 +224,12 @@ static cudaError_t alloc_tables(stencil_plan_s* p) {
 size_t multiplier_table_bytes(int ndim, const int64_t* dims, int precision) {
     const size_t celem = precision == STENCIL_FP32 ? sizeof(float2) : sizeof(double2);
     if (ndim == 3) return periodic_workspace_bytes(ndim, dims, precision);
+    if (ndim == 2 && precision == STENCIL_FP32 && blocked_shape(ndim, dims)) {
+        // the blocked table (or, for implicit plans, the row-major one)
+        const int n_log2 = ilog2_exact(dims[1]) - 1;
+        const size_t blk = (size_t)blocked_item_elems(ilog2_exact(dims[0]), n_log2) * celem;
+        return std::max(blk, periodic_workspace_bytes(ndim, dims, precision));
+    }
     if (ndim == 1) {
         const int64_t n = dims[0] / 2;
         const int64_t cap = 16 * (precision == STENCIL_FP32 ? kMaxThreadsF32 : kMaxThreadsF64);
@@ -274,6 +280,9 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
         ss.p[o] = make_symbol_params(p, len, T, E64, E32, perms ? perms[o] : nullptr);
     for (int i = 0; i < items; ++i) ss.orient[i] = orient ? orient[i] : 0;
     for (int o = 0; o < norient; ++o) ss.vtab[o] = vtabs ? vtabs[o] : nullptr;
+    // a blocked-layout table serves only the blocked passes (set below)
+    const bool blocked_table = vtabs && vtabs[0] && vtabs[0] == p->vt && p->vflags && !p->implicit;
+    if (blocked_table) ss.vtab[0] = nullptr;
     for (int i = 0; i < items; ++i) ss.vtab_item[i] = vitems ? vitems[i] : nullptr;
     const int maxt = sizeof(R) == 4 ? kMaxThreadsF32 : kMaxThreadsF64;
     const int celem = 2 * sizeof(R);
@@ -321,6 +330,10 @@ cudaError_t batched_solve(stencil_plan_s* p, R* S, const int64_t* len, int items
             g.inner_valid = n + 1;
             g.cols_log2 = 13 - l0_log2;
             g.vS = Mp;
+            if (blocked_table && items == 1) {
+                ss.vtab[0] = vtabs[0];
+                ss.vflags = p->vflags;
+            }
             PROF_LAUNCH(PASS_ROWS_R2C, launch_rows_blk(-1, S, H, l0_log2, n_log2, (int)rows, tw,
                                                        twn_log2, status, s));
             PROF_LAUNCH(PASS_COLS_FUSED, launch_cols_tma_blk(H, g, tw, twn_log2, ss, status, s));
@@ -459,6 +472,7 @@ static void free_plan(stencil_plan_s* p) {
     cudaFree(p->status);
     cudaFree(p->dev_grid);
     cudaFree(p->vt);
+    cudaFree(p->vflags);
     cudaFree(p->wq_dev);
     cudaFree(p->wv_dev);
     for (int a = 0; a < 3; ++a) cudaFree(p->mtw[a]);
@@ -597,6 +611,17 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
                 p->dev_bytes += vbytes;
             } else {
                 p->vt = nullptr;
+                cudaGetLastError();
+            }
+        }
+        if (p->vt && ndim == 2 && precision == STENCIL_FP32 && p->gemm < 0 &&
+            blocked_shape(ndim, dims)) {
+            const size_t fb = (size_t)(blocked_item_elems(ilog2_exact(dims[0]),
+                                                          ilog2_exact(dims[1]) - 1) >> 13) * sizeof(int);
+            if (cudaMalloc(&p->vflags, fb) == cudaSuccess) {
+                p->dev_bytes += fb;
+            } else {
+                p->vflags = nullptr;
                 cudaGetLastError();
             }
         }
@@ -762,8 +787,13 @@ int stencil_run(stencil_plan_t p, void* grid, int64_t T, void* stream) {
 // read outweighs the arithmetic it saves), so 2-D evaluates.
 static cudaError_t build_table(stencil_plan_s* p, int64_t T, cudaStream_t s) {
     const SymbolParams sp = make_symbol_params(p, p->dims, T, p->E64, p->E32, nullptr);
-    cudaError_t err = p->precision == STENCIL_FP32 ? launch_vtable<float>(p->vt, sp, p->Mp, s)
-                                                   : launch_vtable<double>(p->vt, sp, p->Mp, s);
+    cudaError_t err;
+    if (p->vflags && !p->implicit)   // FP32 2-D: blocked layout, one flag per column block
+        err = launch_vtable_blk(p->vt, p->vflags, sp, ilog2_exact(p->dims[0]),
+                                ilog2_exact(p->dims[1]) - 1, s);
+    else
+        err = p->precision == STENCIL_FP32 ? launch_vtable<float>(p->vt, sp, p->Mp, s)
+                                           : launch_vtable<double>(p->vt, sp, p->Mp, s);
     if (err == cudaSuccess) p->vt_T = T;
     return err;
 }

@@ -90,6 +90,7 @@ struct stencil_plan_s {
     // plan, cached for vt_T once a second consecutive run asks for the same T
     // (implicit plans: every plan shape, built on the first run of each T)
     void* vt = nullptr;
+    int* vflags = nullptr;   // FP32 2-D blocked plans: vt in the blocked layout, flag per block
     int64_t vt_T = -1;
     int64_t last_T = -1;
     // zero-Dirichlet schedule and buffers (aperiodic.cu)

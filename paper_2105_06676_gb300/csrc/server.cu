@@ -264,6 +264,17 @@ PlanEntry* stencil_server_s::acquire(const Key& k, int* status) {
     for (int a = 0; a < k.ndim; ++a) nw *= 2 * r + 1;
     w0[nw / 2] = 1.0;
     int rc = stencil_plan(&pe->plan, k.ndim, k.dims, r, w0, k.boundary, k.precision);
+    if (rc == STENCIL_OK && pe->plan->vflags) {
+        // every request sets its own weights, so the repeated-T table of a 2-D
+        // plan would rarely be reused: the pool does not hold it
+        stencil_plan_s* p = pe->plan;
+        const int64_t nx = blocked_item_elems(ilog2_exact(p->dims[0]), ilog2_exact(p->dims[1]) - 1) >> 13;
+        p->dev_bytes -= multiplier_table_bytes(p->ndim, p->dims, p->precision) + nx * sizeof(int);
+        cudaFree(p->vt);
+        cudaFree(p->vflags);
+        p->vt = nullptr;
+        p->vflags = nullptr;
+    }
     if (rc == STENCIL_OK && k.batch) {
         const size_t elem = k.precision == STENCIL_FP32 ? 4 : 8;
         int64_t cells = 1;

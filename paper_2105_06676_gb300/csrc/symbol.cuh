@@ -71,6 +71,9 @@ struct SymbolSet {
     const void* vtab[kMaxOrient];
     // optional per-item tables (each item its own weights and T); override vtab
     const void* vtab_item[kMaxItems];
+    // set when vtab[0] is a blocked-layout table (FP32 2-D, one item): one flag
+    // per column block, 0 when every multiplier of the block is zero
+    const int* vflags;
 };
 
 // Per-row multiplier tables of a batched 1-D solve (row r uses t[r] when set).

@@ -158,8 +158,11 @@ def test_size_limits_and_workspace(lib):
     assert lib.stencil_max_axis(1, 1, 0) == 1 << 24
     assert lib.stencil_max_axis(1, 0, 0) == 1 << 24
     d = (ctypes.c_int64 * 2)(4096, 4096)
-    # half spectrum 4096 x (2048 + 1 padded to 2064) complex float
-    assert lib.stencil_workspace_bytes(2, d, 1, 0, 1) == 4096 * 2064 * 8
+    # half spectrum 4096 x (2048 + 1 padded to 2064) complex float, plus the
+    # repeated-T multiplier table (blocked layout; sized for the row-major one
+    # an implicit plan keeps)
+    assert lib.stencil_workspace_bytes(2, d, 1, 0, 1) == 2 * 4096 * 2064 * 8
+    assert lib.stencil_workspace_bytes(2, d, 1, 1, 1) == 4096 * 2064 * 8
     d1 = (ctypes.c_int64 * 1)(4096)
     # 1-D periodic FP64 held by one CTA: no half spectrum, the (2048 + 1)-entry
     # multiplier table kept for a repeated T; zero Dirichlet keeps no such table
