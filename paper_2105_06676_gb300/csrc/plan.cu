@@ -641,6 +641,9 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
             err = cudaMalloc(&p->H, p->H_bytes);
             if (err == cudaSuccess) p->dev_bytes += p->H_bytes;
         }
+        double wsum = 0.0;
+        for (int i = 0; i < p->nweights; ++i) wsum += std::fabs(p->weights[i]);
+        p->vdelta[0] = (float)(wsum * std::ldexp(1.0, -16)) + 1e-30f;
         if (err == cudaSuccess) err = cudaMalloc(&p->wv_dev, p->nweights * sizeof(double));
         if (err == cudaSuccess) {
             p->dev_bytes += p->nweights * sizeof(double);
@@ -719,6 +722,11 @@ int stencil_plan_vector(stencil_plan_t* out, int ndim, const int64_t* dims, int 
     stencil_plan_s* p = *out;
     p->vector = true;
     p->nfields = nfields;
+    for (int b = 0; b < nfields * nfields; ++b) {
+        double sum = 0.0;
+        for (int i = 0; i < nw; ++i) sum += std::fabs(weights[(size_t)b * nw + i]);
+        p->vdelta[b] = (float)(sum * std::ldexp(1.0, -16)) + 1e-30f;
+    }
     // one half spectrum per field (1-D plans keep none of their own); the
     // scalar multiplier table is never used
     cudaFree(p->H);

@@ -65,6 +65,10 @@ struct stencil_plan_s {
     bool vector = false;
     int nfields = 1;
     double* wv_dev = nullptr;
+    // per block: |Lambda_ij - Lambda32_ij| <= sum|w_ij| 2^-16 (a generous
+    // bound on at most 343 products of three rounded table entries and a
+    // rounded weight), for the FP32 underflow screen of the vector multiply
+    float vdelta[16] = {};
     // mixed-radix axes (length not a power of two): exp(-2 pi i m / l_a) per
     // such axis at pass precision; such plans run the vector path with one field
     bool mixed = false;

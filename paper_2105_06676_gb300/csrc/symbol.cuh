@@ -90,7 +90,7 @@ __device__ __forceinline__ C lambda_eval_r(const SymbolParams& p, const C* const
     constexpr int W = 2 * RAD + 1;
     C e0[W], e1[W], e2[W];
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e0[m + RAD] = __ldg(E[0] + (((m * k[0]) & p.tmask[0]) << p.tshift[0]));
+    for (int m = -RAD; m <= RAD; ++m) e0[m + RAD] = __ldg(E[0] + axis_index(p, 0, m * k[0]));
     if (p.ndim == 1) {
         C acc{0, 0};
 #pragma unroll
@@ -98,7 +98,7 @@ __device__ __forceinline__ C lambda_eval_r(const SymbolParams& p, const C* const
         return acc;
     }
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e1[m + RAD] = __ldg(E[1] + (((m * k[1]) & p.tmask[1]) << p.tshift[1]));
+    for (int m = -RAD; m <= RAD; ++m) e1[m + RAD] = __ldg(E[1] + axis_index(p, 1, m * k[1]));
     if (p.ndim == 2) {
         C acc{0, 0};
 #pragma unroll
@@ -111,7 +111,7 @@ __device__ __forceinline__ C lambda_eval_r(const SymbolParams& p, const C* const
         return acc;
     }
 #pragma unroll
-    for (int m = -RAD; m <= RAD; ++m) e2[m + RAD] = __ldg(E[2] + (((m * k[2]) & p.tmask[2]) << p.tshift[2]));
+    for (int m = -RAD; m <= RAD; ++m) e2[m + RAD] = __ldg(E[2] + axis_index(p, 2, m * k[2]));
     C acc{0, 0};
 #pragma unroll
     for (int i = 0; i < W; ++i) {
