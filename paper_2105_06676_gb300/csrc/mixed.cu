@@ -32,30 +32,23 @@ struct RadixPlan {
     int radix[kMaxStages];
 };
 
-// exp(2 pi i q / R) for R = 3, 5, 7, q = 0..R-1 (exact constants, rounded)
-__device__ __forceinline__ double cos_r(int R, int q) {
-    if (R == 3) return q == 0 ? 1.0 : -0.5;
-    if (R == 5) {
-        const double c[5] = {1.0, 0.3090169943749474241023, -0.8090169943749474241023,
-                             -0.8090169943749474241023, 0.3090169943749474241023};
-        return c[q];
-    }
-    const double c[7] = {1.0, 0.6234898018587335305250, -0.2225209339563144042889,
-                         -0.9009688679024191262361, -0.9009688679024191262361,
-                         -0.2225209339563144042889, 0.6234898018587335305250};
-    return c[q];
+// cos / sin(2 pi q / R) for R = 3, 5, 7, q = 0..R-1 (exact constants,
+// rounded); chained conditionals so that constant arguments fold away.
+__host__ __device__ constexpr double cos_r(int R, int q) {
+    return q == 0 ? 1.0
+         : R == 3 ? -0.5
+         : R == 5 ? (q == 1 || q == 4 ? 0.3090169943749474241023 : -0.8090169943749474241023)
+         : (q == 1 || q == 6 ? 0.6234898018587335305250
+            : q == 2 || q == 5 ? -0.2225209339563144042889 : -0.9009688679024191262361);
 }
-__device__ __forceinline__ double sin_r(int R, int q) {
-    if (R == 3) return q == 0 ? 0.0 : q == 1 ? 0.8660254037844386467637 : -0.8660254037844386467637;
-    if (R == 5) {
-        const double s[5] = {0.0, 0.9510565162951535721164, 0.5877852522924731291687,
-                             -0.5877852522924731291687, -0.9510565162951535721164};
-        return s[q];
-    }
-    const double s[7] = {0.0, 0.7818314824680298087084, 0.9749279121818236070181,
-                         0.4338837391175581204758, -0.4338837391175581204758,
-                         -0.9749279121818236070181, -0.7818314824680298087084};
-    return s[q];
+__host__ __device__ constexpr double sin_r(int R, int q) {
+    return q == 0 ? 0.0
+         : R == 3 ? (q == 1 ? 0.8660254037844386467637 : -0.8660254037844386467637)
+         : R == 5 ? (q == 1 ? 0.9510565162951535721164 : q == 2 ? 0.5877852522924731291687
+                     : q == 3 ? -0.5877852522924731291687 : -0.9510565162951535721164)
+         : (q == 1 ? 0.7818314824680298087084 : q == 2 ? 0.9749279121818236070181
+            : q == 3 ? 0.4338837391175581204758 : q == 4 ? -0.4338837391175581204758
+            : q == 5 ? -0.9749279121818236070181 : -0.7818314824680298087084);
 }
 
 // In-register DFT of odd prime size R (3, 5, 7) by its definition:
@@ -86,32 +79,53 @@ __device__ __forceinline__ void dft_any(C* v) {
     else dft_reg<R, DIR>(v);
 }
 
+// x / d and x mod d for 0 <= x < 2^24 through a float reciprocal (rcp = 1/d
+// rounded): the quotient is off by at most one and corrected exactly.
+__device__ __forceinline__ void divmod_small(int x, int d, float rcp, int& q, int& r) {
+    q = __float2int_rz((float)x * rcp);
+    r = x - q * d;
+    if (r < 0) { --q; r += d; }
+    else if (r >= d) { ++q; r -= d; }
+}
+
 // One in-place Stockham stage of radix R over nseq sequences of length n held
 // at sm + s * ss. tw: table of exp(-2 pi i m / (n * twmul)) (read at m *
-// twmul). Contains a CTA barrier.
+// twmul). A butterfly j (k = j mod Ns) loads w = exp(-2 pi i k / (Ns R)) once
+// and forms w^r by products (r <= 7: a few roundings). Contains a CTA barrier.
 template <int R, int DIR, typename C>
 __device__ __forceinline__ void mixed_stage(C* sm, int n, int nseq, int ss, int Ns,
                                             const C* __restrict__ tw, int twmul) {
     constexpr int MAXB = (kMixEPT + R - 1) / R + 1;   // butterflies per thread
     const int nb = n / R;
     const int total = nseq * nb;
-    const int span = n / (Ns * R);   // twiddle index step: m / (Ns R) = m span / n
+    const int span = n / (Ns * R);   // w^k = exp(-2 pi i k span / n)
+    const float rnb = 1.0f / (float)nb, rns = 1.0f / (float)Ns;
     C v[MAXB * R];
+    int pos[MAXB];
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
         const int g = threadIdx.x + b * blockDim.x;
+        pos[b] = -1;
         if (g < total) {
-            const int s = g / nb, j = g - s * nb;
-            const int k = j % Ns;
+            int s, j, jq, k;
+            if (nseq == 1) {
+                s = 0;
+                j = g;
+            } else {
+                divmod_small(g, nb, rnb, s, j);
+            }
+            divmod_small(j, Ns, rns, jq, k);
+            pos[b] = s * ss + jq * Ns * R + k;   // first output position
             const C* src = sm + s * ss;
+            C w1 = tw[k * span * twmul];
+            if (DIR > 0) w1.y = -w1.y;
+            C wr = w1;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 C x = src[j + r * nb];
                 if (r > 0 && k > 0) {
-                    const int m = (k * r * span) % n;
-                    C w = tw[m * twmul];
-                    if (DIR > 0) w.y = -w.y;
-                    x = cmul(x, w);
+                    x = cmul(x, wr);
+                    if (r + 1 < R) wr = cmul(wr, w1);
                 }
                 v[b * R + r] = x;
             }
@@ -121,11 +135,8 @@ __device__ __forceinline__ void mixed_stage(C* sm, int n, int nseq, int ss, int 
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
-        const int g = threadIdx.x + b * blockDim.x;
-        if (g < total) {
-            const int s = g / nb, j = g - s * nb;
-            const int k = j % Ns;
-            C* dst = sm + s * ss + (j - k) * R + k;
+        if (pos[b] >= 0) {
+            C* dst = sm + pos[b];
 #pragma unroll
             for (int r = 0; r < R; ++r) dst[r * Ns] = v[b * R + r];
         }
