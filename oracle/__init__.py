@@ -23,6 +23,10 @@ Contents
 ``recursive_boundary``   StencilFFT-A and RecursiveBoundary in numpy FP64,
                          Sec. 5 and Fig. "stencil-fft-algorithm-1D-aperiodic"
                          (zero-Dirichlet or reflecting base case).
+``ell_shells``           RecursiveBoundary with its regions in l-shells (the
+                         step at which the boundary's influence reaches a
+                         cell, per-face reach of biased stencils), appendix
+                         "l-shell Spatial Grid Decomposition".
 ``implicit``             implicit stencils Q a_{t+1} = S a_t: dense
                          pseudoinverse definition and the spectral method with
                          Lambda_R = Lambda_Q^+ Lambda_S, appendix "Supporting
@@ -53,6 +57,13 @@ from .recursive_boundary import (  # noqa: F401
     boundary_distance,
     recursive_boundary,
     stencil_fft_aperiodic,
+)
+from .ell_shells import (  # noqa: F401
+    arrival_time,
+    face_distances,
+    face_reach,
+    recursive_boundary_shells,
+    stencil_fft_aperiodic_shells,
 )
 from .implicit import (  # noqa: F401
     implicit_dense,
