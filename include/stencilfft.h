@@ -314,15 +314,20 @@ const char* stencil_profile_kind_name(int kind);
 /*
  * Host-only view of the zero-Dirichlet schedule (RecursiveBoundary flattened
  * into a sequence of operations, paper Fig.
- * "stencil-fft-algorithm-1D-aperiodic"), for checking the schedule without a
- * GPU. Writes up to cap int64 values to out (may be NULL) and returns the
- * number needed, or -1 for invalid arguments (radius must be >= 1, T >= 1).
- * Records, in execution order:
- *   1, step, T_k, level, n, then per strip: bdims[3], off[3], valid[3], lo, hi,
- *      face_axis, face_side            -- periodic solves of the strips (stashed)
+ * "stencil-fft-algorithm-1D-aperiodic", with its regions over l-shells,
+ * appendix "l-shell Spatial Grid Decomposition"), for checking the schedule
+ * without a GPU. Writes up to cap int64 values to out (may be NULL) and
+ * returns the number needed, or -1 for invalid arguments (radius must be >= 1,
+ * T >= 1). Faces are numbered f = 2 a + side (side 0: the face below index 0
+ * of axis a, distance g_a + 1; side 1: the face above index l_a - 1, distance
+ * l_a - g_a). Records, in execution order:
+ *   1, step, T_k, level, n, then per strip: bdims[3], off[3], valid[3],
+ *      perm[3], lo[6], hi[6], face_axis, face_side
+ *                                      -- periodic solves of the strips (stashed)
  *   2, step                            -- scatter of that step's kept cells
- *   3, T_b, n, then per tile: (lo, hi) for each of 3 axes
- *                                      -- base case over output tiles
+ *   3, T_b, wout[6], n, then per tile: (lo, hi) for each of 3 axes
+ *                                      -- base case over output tiles, writing
+ *                                         the cells within wout[f] of some face f
  *   4, T_c                             -- T_c steps of the loop on the whole grid
  *   5, T                               -- T single steps of the loop on the whole grid
  *   6, T                               -- T steps of the loop on the whole grid held
@@ -330,12 +335,20 @@ const char* stencil_profile_kind_name(int kind);
  *                                         (only where a GPU that can run it is present)
  * With cutoff 0 the schedule is the one the solver runs: RecursiveBoundary, or
  * the plain loop (records 4 / 5 / 6 only) when its estimated cost is lower.
- * Axes beyond ndim are reported with extent 1. A strip's box cell q maps to
- * grid cell off + q when q < valid on every axis; a scatter writes the cells
- * with lo < dist <= hi and, when face_axis >= 0, distance to that face <= hi.
+ * Axes beyond ndim are reported with extent 1 and faces beyond 2 ndim with 0.
+ * A strip's box axis b is grid axis perm[b]; its box cell q maps to grid cell
+ * off + q when q < valid on every axis. A scatter writes the cells farther
+ * than lo[f] from every face f that are within hi[f] of the strip's own face
+ * (face_axis, face_side), or of some face when face_axis is -1 (a whole-grid
+ * solve). stencil_debug_schedule takes the toward-reach of every face to be
+ * radius (a (2 radius + 1)^ndim box of nonzero weights);
+ * stencil_debug_schedule_reach takes reach[2 a + side] (each in 0..radius, not
+ * all 0): the largest offset towards that face among the nonzero weights.
  */
 int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_t T,
                                int64_t cutoff, int64_t* out, int64_t cap);
+int64_t stencil_debug_schedule_reach(int ndim, const int64_t* dims, int radius, const int* reach,
+                                     int64_t T, int64_t cutoff, int64_t* out, int64_t cap);
 
 /*
  * Periodic solve that allocates nothing. The paper has no counterpart: this

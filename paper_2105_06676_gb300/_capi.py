@@ -60,6 +60,8 @@ SIGNATURES = [
     ("stencil_noalloc_scratch_bytes", _c.c_size_t, []),
     ("stencil_debug_schedule", _c.c_int64, [_c.c_int, _i64p, _c.c_int, _c.c_int64, _c.c_int64,
                                             _i64p, _c.c_int64]),
+    ("stencil_debug_schedule_reach", _c.c_int64, [_c.c_int, _i64p, _c.c_int, _c.POINTER(_c.c_int),
+                                                  _c.c_int64, _c.c_int64, _i64p, _c.c_int64]),
 ]
 
 class StencilRequest(ctypes.Structure):

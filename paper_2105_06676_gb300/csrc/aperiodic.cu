@@ -72,15 +72,30 @@ struct ItemGeom {
     int face_side;
 };
 
+// Faces are numbered f = 2 a + side; the distance of cell g to face f is
+// g_a + 1 (side 0) or l_a - g_a (side 1). A scatter writes the cells that are
+// clear of every face (distance > lo[f] for all f) and within hi[f] of some
+// face f (of its own face for a strip).
 struct BatchGeom {
     int ndim;
     int gdims[3];
     int bdims[3];
     long long box_cells;
     int items;
-    int lo, hi;      // a scatter writes lo < dist <= hi (and face distance <= hi)
+    int lo[6], hi[6];
     ItemGeom it[kMaxItems];
 };
+
+// Some face f of the first ndim axes with distance(g, f) <= w[f].
+__device__ __forceinline__ bool near_face(const int* g, const int* gd, int ndim, const int* w) {
+    bool n = false;
+    for (int a = 0; a < ndim; ++a) n |= (g[a] + 1 <= w[2 * a]) | (gd[a] - g[a] <= w[2 * a + 1]);
+    return n;
+}
+
+__device__ __forceinline__ int face_distance(const int* g, const int* gd, int f) {
+    return (f & 1) ? gd[f >> 1] - g[f >> 1] : g[f >> 1] + 1;
+}
 
 __device__ __forceinline__ bool item_cell(const BatchGeom& b, long long e, int* item, int* g) {
     *item = (int)(e / b.box_cells);
@@ -120,14 +135,13 @@ __global__ void k_scatter(const R* __restrict__ S, R* __restrict__ X,
          e += (long long)gridDim.x * blockDim.x) {
         int item, g[3];
         if (!item_cell(b, e, &item, g)) continue;
-        int d = 0x7fffffff;
-        for (int a = 0; a < b.ndim; ++a) d = min(d, min(g[a] + 1, b.gdims[a] - g[a]));
-        if (d <= b.lo || d > b.hi) continue;
+        if (near_face(g, b.gdims, b.ndim, b.lo)) continue;
         const ItemGeom& it = b.it[item];
         if (it.face_axis >= 0) {
-            const int a = it.face_axis;
-            const int df = it.face_side == 0 ? g[a] + 1 : b.gdims[a] - g[a];
-            if (df > b.hi) continue;
+            const int f = 2 * it.face_axis + it.face_side;
+            if (face_distance(g, b.gdims, f) > b.hi[f]) continue;
+        } else if (!near_face(g, b.gdims, b.ndim, b.hi)) {
+            continue;
         }
         X[grid_index(g, b)] = S[e];
     }
@@ -145,7 +159,7 @@ struct BaseParams {
     int gdims[3];
     int Tb;
     int mirror;       // reflecting boundary: ghosts mirror the cells inside (else zero)
-    int wout;         // write cells with dist <= wout
+    int wout[6];      // write cells within wout[f] of some face f
     double w[kMaxWeights];
     float wf[kMaxWeights];
 };
@@ -226,9 +240,7 @@ k_base_tiles(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restr
     const int ovol = ox * oy * oz;
     for (int e = threadIdx.x; e < ovol; e += blockDim.x) {
         int g3[3] = {olo[0] + e / (ox * oy), olo[1] + (e / ox) % oy, olo[2] + e % ox};
-        int d = 0x7fffffff;
-        for (int a = 3 - p.ndim; a < 3; ++a) d = min(d, min(g3[a] + 1, gd[a] - g3[a]));
-        if (d > p.wout) continue;
+        if (!near_face(g3 + off, gd + off, p.ndim, p.wout)) continue;
         const int z = g3[0] - ilo[0], y = g3[1] - ilo[1], x = g3[2] - ilo[2];
         const long long gi = ((long long)g3[0] * gd[1] + g3[1]) * gd[2] + g3[2];
         Y[gi] = b0[(z * ext[1] + y) * ext[2] + x];
@@ -249,9 +261,7 @@ __global__ void k_tile_copy(const R* __restrict__ Y, R* __restrict__ X,
     const int ox = hi[2] - lo[2], oy = hi[1] - lo[1], oz = hi[0] - lo[0];
     for (int e = threadIdx.x; e < ox * oy * oz; e += blockDim.x) {
         int g3[3] = {lo[0] + e / (ox * oy), lo[1] + (e / ox) % oy, lo[2] + e % ox};
-        int d = 0x7fffffff;
-        for (int a = off; a < 3; ++a) d = min(d, min(g3[a] + 1, gd[a] - g3[a]));
-        if (d > p.wout) continue;
+        if (!near_face(g3 + off, gd + off, p.ndim, p.wout)) continue;
         const long long gi = ((long long)g3[0] * gd[1] + g3[1]) * gd[2] + g3[2];
         X[gi] = Y[gi];
     }
@@ -382,8 +392,8 @@ k_base_2d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
     const int oy = t.hi[0] - t.lo[0], ox = t.hi[1] - t.lo[1];
     for (int e = threadIdx.x; e < oy * ox; e += blockDim.x) {
         const int gy = t.lo[0] + e / ox, gx = t.lo[1] + e % ox;
-        const int d = min(min(gy + 1, L0 - gy), min(gx + 1, L1 - gx));
-        if (d > p.wout) continue;
+        const int g2[2] = {gy, gx};
+        if (!near_face(g2, p.gdims, 2, p.wout)) continue;
         Y[(long long)gy * L1 + gx] = b0[(gy - iy0 + RAD) * pitch + gx - ix0 + RAD];
     }
 }
@@ -430,8 +440,7 @@ k_base_1d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
         b1 = tmp;
     }
     for (int g = t.lo[0] + threadIdx.x; g < t.hi[0]; g += blockDim.x) {
-        const int d = min(g + 1, L - g);
-        if (d <= p.wout) Y[g] = b0[g - i0 + RAD];
+        if (g + 1 <= p.wout[0] || L - g <= p.wout[1]) Y[g] = b0[g - i0 + RAD];
     }
 }
 
@@ -508,8 +517,8 @@ k_base_3d(const R* __restrict__ X, R* __restrict__ Y, const BaseTile* __restrict
     for (int zy = ty; zy < oz * oy; zy += ny) {
         const int gz = t.lo[0] + zy / oy, gy = t.lo[1] + zy % oy;
         for (int gx = t.lo[2] + tx; gx < t.hi[2]; gx += 32) {
-            const int d = min(min(min(gz + 1, L0 - gz), min(gy + 1, L1 - gy)), min(gx + 1, L2 - gx));
-            if (d > p.wout) continue;
+            const int g3[3] = {gz, gy, gx};
+            if (!near_face(g3, p.gdims, 3, p.wout)) continue;
             Y[((long long)gz * L1 + gy) * L2 + gx] =
                 b0[(gz - lo[0] + RAD) * plane + (gy - lo[1] + RAD) * px + gx - lo[2] + RAD];
         }
@@ -775,23 +784,22 @@ k_copy_2d(R* __restrict__ X, R* __restrict__ S, const __grid_constant__ BatchGeo
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const bool transposed = it.perm[0] == 1;
     if (SCATTER && it.face_axis >= 0) {
-        // kept cells have face distance in (lo, hi]; the face normal is box
-        // axis 0, so only box rows in that band can be written
+        // kept cells have distance to the strip's face in (lo[f], hi[f]]; the
+        // face normal is box axis 0, so only box rows in that band can be written
         const int a = it.face_axis, offn = it.off[a], Ln = a == 0 ? L0 : L1;
-        const int klo = it.face_side == 0 ? b.lo - offn : Ln - offn - b.hi;
-        const int khi = it.face_side == 0 ? b.hi - offn : Ln - offn - b.lo;
+        const int f = 2 * a + it.face_side;
+        const int klo = it.face_side == 0 ? b.lo[f] - offn : Ln - offn - b.hi[f];
+        const int khi = it.face_side == 0 ? b.hi[f] - offn : Ln - offn - b.lo[f];
         if (q0b >= khi || q0b + 32 <= klo) return;
     }
     auto keep = [&](int g0, int g1) {
-        const int d = min(min(g0 + 1, L0 - g0), min(g1 + 1, L1 - g1));
-        if (d <= b.lo || d > b.hi) return false;
+        const int g[2] = {g0, g1};
+        if (near_face(g, b.gdims, 2, b.lo)) return false;
         if (it.face_axis >= 0) {
-            const int gf = it.face_axis == 0 ? g0 : g1;
-            const int Lf = it.face_axis == 0 ? L0 : L1;
-            const int df = it.face_side == 0 ? gf + 1 : Lf - gf;
-            if (df > b.hi) return false;
+            const int f = 2 * it.face_axis + it.face_side;
+            return face_distance(g, b.gdims, f) <= b.hi[f];
         }
-        return true;
+        return near_face(g, b.gdims, 2, b.hi);
     };
     if (!transposed) {
         for (int r = ty; r < 32; r += 8) {
@@ -845,8 +853,8 @@ k_tile_copy_2d(const R* __restrict__ Y, R* __restrict__ X, const BaseTile* __res
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int y = t.lo[0] + ty; y < t.hi[0]; y += 8)
         for (int x = t.lo[1] + tx; x < t.hi[1]; x += 32) {
-            const int d = min(min(y + 1, L0 - y), min(x + 1, L1 - x));
-            if (d > p.wout) continue;
+            const int g2[2] = {y, x};
+            if (!near_face(g2, p.gdims, 2, p.wout)) continue;
             const long long gi = (long long)y * L1 + x;
             X[gi] = Y[gi];
         }
@@ -947,14 +955,54 @@ static int box_Mp(int64_t n, int precision) {
     return (int)((n + 1 + align - 1) / align * align);
 }
 
-// The strips of a periodic solve over the region dist <= W keeping (lo, hi],
-// grouped into batches of equal box shape.
-static std::vector<Batch> make_batches(const stencil_plan_s* p, int64_t W, int lo, int hi) {
+// l-shells (appendix "l-shell Spatial Grid Decomposition"): face f = 2 a + side
+// is looked towards by reach_to(f) cells per step (its toward-reach) and away
+// from by reach_from(f) = the opposite face's toward-reach. After t steps the
+// boundary has reached exactly the cells within reach_to(f) t of some face f; a
+// kept cell's dependence cone over t steps reaches reach_to(f) t towards and
+// reach_from(f) t away from every face. A face with toward-reach 0 never
+// reaches any cell: it gets no strip and no band.
+static int reach_to(const stencil_plan_s* p, int f) { return p->reach[f >> 1][f & 1]; }
+static int reach_from(const stencil_plan_s* p, int f) { return p->reach[f >> 1][(f & 1) ^ 1]; }
+
+// Per-face bounds of a region or keep range: v[f] = reach_to(f) x + reach_from(f) y
+// (0 for faces that no offset looks towards), capped at kNoHi.
+struct FaceBounds {
+    int64_t v[6] = {0, 0, 0, 0, 0, 0};
+};
+static FaceBounds face_bounds(const stencil_plan_s* p, int64_t x, int64_t y) {
+    FaceBounds b;
+    for (int f = 0; f < 2 * p->ndim; ++f)
+        b.v[f] = reach_to(p, f) > 0
+                     ? std::min<int64_t>(reach_to(p, f) * x + reach_from(p, f) * y, kNoHi)
+                     : 0;
+    return b;
+}
+// Some cell lies farther than lo.v[f] from every face f.
+static bool clear_cells_exist(const stencil_plan_s* p, const FaceBounds& lo) {
+    for (int a = 0; a < p->ndim; ++a)
+        if (lo.v[2 * a] + lo.v[2 * a + 1] >= p->dims[a]) return false;
+    return true;
+}
+static bool any_reach(const stencil_plan_s* p) {
+    for (int f = 0; f < 2 * p->ndim; ++f)
+        if (reach_to(p, f) > 0) return true;
+    return false;
+}
+
+// The strips of a periodic solve over the region "within W.v[f] of some face f"
+// keeping the cells clear of every face by lo and within hi of their strip's
+// face, grouped into batches of equal box shape.
+static std::vector<Batch> make_batches(const stencil_plan_s* p, const FaceBounds& W,
+                                       const FaceBounds& lo, const FaceBounds& hi) {
     const int d = p->ndim;
-    const int64_t P = next_pow2(std::max<int64_t>({W, 4, 2 * p->radius + 1}));
+    int64_t P[6] = {0, 0, 0, 0, 0, 0};
+    for (int f = 0; f < 2 * d; ++f)
+        if (reach_to(p, f) > 0)
+            P[f] = next_pow2(std::max<int64_t>({W.v[f], 4, 2 * p->radius + 1}));
     bool whole = false;
     for (int a = 0; a < d; ++a)
-        if (2 * P >= p->dims[a]) whole = true;
+        if (P[2 * a] + P[2 * a + 1] >= p->dims[a]) whole = true;
     struct Item { int64_t bdims[3]; ItemGeom g; };
     std::vector<Item> items;
     if (whole) {
@@ -971,6 +1019,8 @@ static std::vector<Batch> make_batches(const stencil_plan_s* p, int64_t W, int l
     } else {
         for (int a = 0; a < d; ++a) {
             for (int side = 0; side < 2; ++side) {
+                const int f = 2 * a + side;
+                if (reach_to(p, f) == 0) continue;
                 Item it;
                 int perm[3] = {a, 0, 0}, k = 1;
                 for (int b = 0; b < d; ++b)
@@ -980,14 +1030,14 @@ static std::vector<Batch> make_batches(const stencil_plan_s* p, int64_t W, int l
                     it.g.perm[b] = perm[b];
                     it.g.off[b] = 0;
                 }
-                it.g.off[a] = side == 0 ? 0 : (int)(p->dims[a] - W);
+                it.g.off[a] = side == 0 ? 0 : (int)(p->dims[a] - W.v[f]);
                 for (int b = 0; b < 3; ++b) {
                     if (b >= d) {
                         it.bdims[b] = 1;
                         it.g.valid[b] = 1;
                     } else if (b == 0) {
-                        it.bdims[b] = P;
-                        it.g.valid[b] = (int)W;
+                        it.bdims[b] = P[f];
+                        it.g.valid[b] = (int)W.v[f];
                     } else {
                         it.bdims[b] = p->dims[perm[b]];
                         it.g.valid[b] = (int)p->dims[perm[b]];
@@ -1018,8 +1068,10 @@ static std::vector<Batch> make_batches(const stencil_plan_s* p, int64_t W, int l
                 b->geom.bdims[a] = (int)it.bdims[a];
                 b->geom.box_cells *= it.bdims[a];
             }
-            b->geom.lo = lo;
-            b->geom.hi = hi;
+            for (int f = 0; f < 6; ++f) {
+                b->geom.lo[f] = (int)lo.v[f];
+                b->geom.hi[f] = (int)hi.v[f];
+            }
             b->norient = 0;
         }
         int o = 0;
@@ -1034,37 +1086,40 @@ static std::vector<Batch> make_batches(const stencil_plan_s* p, int64_t W, int l
     return out;
 }
 
+// RecursiveBoundary(T) over l-shells, with a = reach_to(f), b = reach_from(f)
+// per face (a = b = sigma on every face gives the distance form of the header):
+// input "within (a + b) T of some face", output "within a T of some face";
+// Step 1 keeps the cells clear of every face by a T1 and within a T + b T2 of
+// some face, Step 2 those clear by a T2 and within a T. A kept cell's cone
+// reaches b T_k away from its face, which the solve's region holds.
 static void build_rb(const stencil_plan_s* p, Schedule& sc, int64_t T, int level, int64_t cutoff) {
-    const int sigma = p->radius;
     if (T < cutoff) {
         sc.ops.push_back(Op{Op::BASE, -1, T});
         return;
     }
     const int64_t T1 = T / 2, T2 = T - T1;
-    // the largest dist in the grid: a keep range starting at or above it is empty
-    int64_t maxdist = p->dims[0] - p->dims[0] / 2;
-    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] - p->dims[a] / 2);
-    // Step 1: P1 over dist <= 2 sigma T for T1 steps, kept on (sigma T1, sigma T + sigma T2]
+    // Step 1: P1 over the input region for T1 steps, kept clear by a T1 and within a T + b T2
     int i1 = -1;
-    if (sigma * T1 < maxdist) {
+    const FaceBounds lo1 = face_bounds(p, T1, 0);
+    if (clear_cells_exist(p, lo1)) {
         Step s1;
         s1.level = level;
         s1.T = T1;
-        s1.batches = make_batches(p, 2 * sigma * T, (int)(sigma * T1),
-                                  (int)std::min<int64_t>(sigma * T + sigma * T2, kNoHi));
+        s1.batches = make_batches(p, face_bounds(p, T, T), lo1, face_bounds(p, T, T2));
         sc.steps.push_back(s1);
         i1 = (int)sc.steps.size() - 1;
         sc.ops.push_back(Op{Op::SOLVE, i1, 0});
     }
     build_rb(p, sc, T1, level + 1, cutoff);
     if (i1 >= 0) sc.ops.push_back(Op{Op::SCATTER, i1, 0});
-    // Step 2: P2 over dist <= sigma T + sigma T2 for T2 steps, kept on (sigma T2, sigma T]
+    // Step 2: P2 over "within a T + b T2" for T2 steps, kept clear by a T2 and within a T
     int i2 = -1;
-    if (sigma * T2 < maxdist) {
+    const FaceBounds lo2 = face_bounds(p, T2, 0);
+    if (clear_cells_exist(p, lo2)) {
         Step s2;
         s2.level = level;
         s2.T = T2;
-        s2.batches = make_batches(p, sigma * T + sigma * T2, (int)(sigma * T2), (int)(sigma * T));
+        s2.batches = make_batches(p, face_bounds(p, T, T2), lo2, face_bounds(p, T, 0));
         sc.steps.push_back(s2);
         i2 = (int)sc.steps.size() - 1;
         sc.ops.push_back(Op{Op::SOLVE, i2, 0});
@@ -1153,12 +1208,15 @@ static cudaError_t ensure_level(AperiodicState* st, int level, size_t sb, size_t
     return cudaSuccess;
 }
 
-// Output tiles of the frame dist <= w for the base case.
+// Output tiles of the base case's frame, the cells within reach_to(f) T_b of
+// some face f (bands per face, earlier axes' bands excluded); the loop reads a
+// halo of radius x T_b around each tile.
 static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb, size_t* smem,
                                             bool whole_grid) {
     const int d = p->ndim;
-    const int w = (int)(p->radius * Tb);
-    const int h = w;
+    int w[6] = {0, 0, 0, 0, 0, 0};
+    for (int f = 0; f < 2 * d; ++f) w[f] = (int)std::min<int64_t>(reach_to(p, f) * Tb, kNoHi);
+    const int h = (int)(p->radius * Tb);
     const size_t budget = 150 * 1024 / (2 * p->elem);  // cells per buffer
     std::vector<BaseTile> tiles;
     // regions: bands per face, earlier axes' bands excluded
@@ -1166,7 +1224,7 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
     std::vector<Region> regions;
     bool whole = whole_grid;
     for (int a = 0; a < d; ++a)
-        if (2 * (int64_t)w >= p->dims[a]) whole = true;
+        if ((int64_t)w[2 * a] + w[2 * a + 1] >= p->dims[a]) whole = true;
     if (whole) {
         Region r;
         for (int a = 0; a < 3; ++a) { r.lo[a] = 0; r.hi[a] = a < d ? (int)p->dims[a] : 1; }
@@ -1175,17 +1233,19 @@ static std::vector<BaseTile> make_base_tiles(const stencil_plan_s* p, int64_t Tb
     } else {
         for (int a = 0; a < d; ++a) {
             for (int side = 0; side < 2; ++side) {
+                const int wf = w[2 * a + side];
+                if (wf == 0) continue;
                 Region r;
                 r.normal = a;
                 bool empty = false;
                 for (int b = 0; b < 3; ++b) {
                     if (b >= d) { r.lo[b] = 0; r.hi[b] = 1; continue; }
                     if (b == a) {
-                        r.lo[b] = side == 0 ? 0 : (int)p->dims[b] - w;
-                        r.hi[b] = side == 0 ? w : (int)p->dims[b];
+                        r.lo[b] = side == 0 ? 0 : (int)p->dims[b] - wf;
+                        r.hi[b] = side == 0 ? wf : (int)p->dims[b];
                     } else if (b < a) {
-                        r.lo[b] = w;
-                        r.hi[b] = (int)p->dims[b] - w;
+                        r.lo[b] = w[2 * b];
+                        r.hi[b] = (int)p->dims[b] - w[2 * b + 1];
                         if (r.hi[b] <= r.lo[b]) empty = true;
                     } else {
                         r.lo[b] = 0;
@@ -1256,7 +1316,9 @@ static cudaError_t launch_base(stencil_plan_s* p, const BaseSet& bs, R* X, R* Y,
     for (int a = 0; a < p->ndim; ++a) bp.gdims[a] = (int)p->dims[a];
     bp.Tb = (int)Tb;
     bp.mirror = p->boundary == STENCIL_NEUMANN ? 1 : 0;
-    bp.wout = whole ? 0x3fffffff : (int)(p->radius * Tb);
+    for (int f = 0; f < 6; ++f)
+        bp.wout[f] = whole ? kNoHi
+                           : f < 2 * p->ndim ? (int)std::min<int64_t>(reach_to(p, f) * Tb, kNoHi) : 0;
     for (int i = 0; i < p->nweights; ++i) {
         bp.w[i] = p->weights[i];
         bp.wf[i] = (float)p->weights[i];
@@ -1419,9 +1481,8 @@ static double tile_cells_effective(const stencil_plan_s* p, const std::vector<Ba
 
 static double schedule_cost(const stencil_plan_s* p, const Schedule& sc, int64_t T) {
     double c = 0.0;
-    int64_t maxdist = p->dims[0] / 2;
-    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
-    if (p->radius * T < maxdist) c += (double)p->n_cells * fft_cell_s(p);   // interior solve
+    if (clear_cells_exist(p, face_bounds(p, T, 0)))
+        c += (double)p->n_cells * fft_cell_s(p);   // interior solve
     // a strip batch: gather, three or five FFT passes, table and scatter
     // launches and the step's stream joins, about 20 us of fixed cost (100 us
     // for 1-D, whose strips are tiny next to it); 2-D leaves run about 5x
@@ -1851,8 +1912,11 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
             b.it[0].valid[a] = (int)p->dims[a];
         }
         b.it[0].face_axis = -1;
-        b.lo = (int)(p->radius * T);
-        b.hi = kNoHi;
+        const FaceBounds lo = face_bounds(p, T, 0);
+        for (int f = 0; f < 6; ++f) {
+            b.lo[f] = (int)lo.v[f];
+            b.hi[f] = kNoHi;
+        }
         p->prof.begin(PASS_COPY, main);
         k_scatter<R><<<grid_blocks(p->n_cells), 256, 0, main>>>(Z, X, b, p->n_cells);
         err = cudaGetLastError();
@@ -1866,9 +1930,7 @@ static cudaError_t emit(stencil_plan_s* p, AperiodicState* st, const Schedule& s
 static cudaError_t prepare_all(stencil_plan_s* p, int64_t T, Schedule** out) {
     cudaError_t err = prepare(p, T, out);
     if (err != cudaSuccess) return err;
-    int64_t maxdist = p->dims[0] / 2;
-    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
-    const bool interior = !(*out)->loop && p->radius * T < maxdist;
+    const bool interior = !(*out)->loop && clear_cells_exist(p, face_bounds(p, T, 0));
     AperiodicState* st = p->ap;
     if (interior && !st->Z) {
         err = cudaMalloc(&st->Z, (size_t)p->n_cells * p->elem);
@@ -1883,16 +1945,13 @@ static cudaError_t prepare_all(stencil_plan_s* p, int64_t T, Schedule** out) {
 
 template <typename R>
 static cudaError_t aperiodic_impl(stencil_plan_s* p, R* grid, int64_t T, cudaStream_t s) {
-    const int sigma = p->radius;
-    if (sigma == 0)  // a pointwise stencil never feels the boundary
+    if (p->radius == 0 || !any_reach(p))   // a pointwise stencil never feels the boundary
         return periodic_solve<R>(p, grid, p->dims, T, p->H, p->Mp, p->tw, p->twn_log2, p->E64,
                                  p->E32, p->status, s);
-    int64_t maxdist = p->dims[0] / 2;
-    for (int a = 1; a < p->ndim; ++a) maxdist = std::min(maxdist, p->dims[a] / 2);
     Schedule* sc = nullptr;
     cudaError_t err = prepare_all(p, T, &sc);
     if (err != cudaSuccess) return err;
-    const bool interior = !sc->loop && sigma * T < maxdist;
+    const bool interior = !sc->loop && clear_cells_exist(p, face_bounds(p, T, 0));
     AperiodicState* st = p->ap;
     // profiled runs: one stream, every launch bracketed by events
     if (p->prof.enabled) return emit<R>(p, st, *sc, grid, T, interior, s, false);
@@ -2024,7 +2083,7 @@ int aperiodic_run(stencil_plan_s* p, void* grid, int64_t T, cudaStream_t s) {
 }
 
 int aperiodic_prepare(stencil_plan_s* p, int64_t T) {
-    if (p->radius == 0) return STENCIL_OK;   // solved by the periodic path
+    if (p->radius == 0 || !any_reach(p)) return STENCIL_OK;   // solved by the periodic path
     Schedule* sc = nullptr;
     const cudaError_t err = prepare_all(p, T, &sc);
     if (err == cudaSuccess) return STENCIL_OK;
@@ -2059,8 +2118,9 @@ void aperiodic_release(stencil_plan_s* p) {
 }
 
 // Host-only export of the zero-Dirichlet schedule (see stencilfft.h).
-extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_t T,
-                                          int64_t cutoff, int64_t* out, int64_t cap) {
+extern "C" int64_t stencil_debug_schedule_reach(int ndim, const int64_t* dims, int radius,
+                                                const int* reach, int64_t T, int64_t cutoff,
+                                                int64_t* out, int64_t cap) {
     if (ndim < 1 || ndim > 3 || !dims || radius < 1 || radius > kMaxRadius || T < 1 ||
         (cutoff != 0 && cutoff < 2))
         return -1;
@@ -2073,7 +2133,13 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
     for (int a = 0; a < ndim; ++a) {
         if (dims[a] < 4 || ilog2_exact(dims[a]) < 0) return -1;
         p.dims[a] = dims[a];
+        for (int side = 0; side < 2; ++side) {
+            const int v = reach ? reach[2 * a + side] : radius;
+            if (v < 0 || v > radius) return -1;
+            p.reach[a][side] = v;
+        }
     }
+    if (!any_reach(&p)) return -1;
     p.n_cells = 1;
     for (int a = 0; a < ndim; ++a) p.n_cells *= dims[a];
     p.nweights = 1;
@@ -2097,6 +2163,8 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
             std::vector<BaseTile> tiles = make_base_tiles(&p, op.T, &smem);
             v.push_back(3);
             v.push_back(op.T);
+            for (int f = 0; f < 6; ++f)
+                v.push_back(f < 2 * ndim ? std::min<int64_t>(reach_to(&p, f) * op.T, kNoHi) : 0);
             v.push_back((int64_t)tiles.size());
             for (const BaseTile& t : tiles)
                 for (int a = 0; a < 3; ++a) {
@@ -2125,8 +2193,8 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
                 for (int a = 0; a < 3; ++a) v.push_back(g.off[a]);
                 for (int a = 0; a < 3; ++a) v.push_back(g.valid[a]);
                 for (int a = 0; a < 3; ++a) v.push_back(g.perm[a]);
-                v.push_back(b.geom.lo);
-                v.push_back(b.geom.hi);
+                for (int f = 0; f < 6; ++f) v.push_back(b.geom.lo[f]);
+                for (int f = 0; f < 6; ++f) v.push_back(b.geom.hi[f]);
                 v.push_back(g.face_axis);
                 v.push_back(g.face_side);
             }
@@ -2135,4 +2203,9 @@ extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int rad
     if (out && cap > 0)
         for (int64_t i = 0; i < (int64_t)v.size() && i < cap; ++i) out[i] = v[i];
     return (int64_t)v.size();
+}
+
+extern "C" int64_t stencil_debug_schedule(int ndim, const int64_t* dims, int radius, int64_t T,
+                                          int64_t cutoff, int64_t* out, int64_t cap) {
+    return stencil_debug_schedule_reach(ndim, dims, radius, nullptr, T, cutoff, out, cap);
 }

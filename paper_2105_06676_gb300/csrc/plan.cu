@@ -586,6 +586,7 @@ int stencil_plan(stencil_plan_t* out, int ndim, const int64_t* dims, int radius,
         p->weights[i] = weights[i];
     }
     p->real_symbol = symmetric_weights(p->weights, ndim, radius);
+    face_reach(p->weights, ndim, radius, p->reach);
     p->elem = precision == STENCIL_FP32 ? sizeof(float) : sizeof(double);
     p->n_cells = 1;
     for (int a = 0; a < ndim; ++a) p->n_cells *= dims[a];
@@ -940,12 +941,33 @@ extern "C" {
 namespace sfft {
 // Replace a plan's weights (same radius bound); captured graphs hold the old
 // weights in their kernel parameters and are dropped.
+// Weight (m_0 + r, .., m_{d-1} + r) (row-major, axis 0 slowest) multiplies
+// a_t[i + m]: the face below index 0 of axis a is looked towards by -m_a, the
+// face above the last index by +m_a.
+void face_reach(const double* w, int ndim, int radius, int reach[3][2]) {
+    const int W = 2 * radius + 1;
+    int n = 1;
+    for (int a = 0; a < ndim; ++a) n *= W;
+    for (int a = 0; a < 3; ++a) reach[a][0] = reach[a][1] = 0;
+    for (int i = 0; i < n; ++i) {
+        if (w[i] == 0.0) continue;
+        int rest = i;
+        for (int a = ndim - 1; a >= 0; --a) {
+            const int m = rest % W - radius;
+            rest /= W;
+            reach[a][0] = std::max(reach[a][0], -m);
+            reach[a][1] = std::max(reach[a][1], m);
+        }
+    }
+}
+
 void plan_set_weights(stencil_plan_s* p, int radius, const double* w) {
     p->radius = radius;
     p->nweights = 1;
     for (int a = 0; a < p->ndim; ++a) p->nweights *= 2 * radius + 1;
     for (int i = 0; i < p->nweights; ++i) p->weights[i] = w[i];
     p->real_symbol = symmetric_weights(p->weights, p->ndim, radius);
+    face_reach(p->weights, p->ndim, radius, p->reach);
     p->vt_T = -1;   // the cached multipliers belong to the old weights
     p->last_T = -1;
     aperiodic_forget_graphs(p);
@@ -962,7 +984,11 @@ extern "C" int stencil_plan_set_weights(stencil_plan_t p, int radius, const doub
     }
     for (int i = 0; i < nw; ++i)
         if (!std::isfinite(weights[i])) return STENCIL_EINVAL;
-    if (radius != p->radius) aperiodic_forget_schedules(p);   // the schedule depends on sigma
+    // the schedule depends on sigma and on the reach towards every face
+    int reach[3][2];
+    face_reach(weights, p->ndim, radius, reach);
+    if (radius != p->radius || std::memcmp(reach, p->reach, sizeof(reach)) != 0)
+        aperiodic_forget_schedules(p);
     plan_set_weights(p, radius, weights);
     return STENCIL_OK;
 }

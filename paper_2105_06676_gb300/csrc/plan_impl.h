@@ -55,6 +55,10 @@ struct stencil_plan_s {
     double weights[sfft::kMaxWeights] = {};
     int nweights = 0;
     bool real_symbol = false;
+    // toward-reach per face [axis][side] (side 0: the face below index 0): the
+    // largest offset towards that face among the nonzero weights; it sets the
+    // l-shell regions of the zero-Dirichlet / reflecting solves
+    int reach[3][2] = {};
     // implicit stencil Q a_{t+1} = S a_t (weights hold S): Q's weights, also
     // in device memory for the multiplier-table kernel
     bool implicit = false;
@@ -116,6 +120,8 @@ void note_cuda_error(cudaError_t err);
 void plan_free_idle(stencil_plan_s* p);
 int ilog2_exact(int64_t v);
 void plan_set_weights(stencil_plan_s* p, int radius, const double* w);
+// toward-reach per face of (2 radius + 1)^ndim weights into reach[3][2]
+void face_reach(const double* w, int ndim, int radius, int reach[3][2]);
 int64_t max_axis(int ndim, int precision, int axis);
 SymbolParams make_symbol_params(const stencil_plan_s* p, const int64_t* len, int64_t T,
                                 const double2* const* E64, const float2* const* E32,

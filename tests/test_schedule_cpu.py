@@ -17,6 +17,7 @@ import pytest
 
 import __graft_entry__
 import oracle
+from oracle import ell_shells as es
 from paper_2105_06676_gb300 import _capi
 from paper_2105_06676_gb300 import workloads as wl
 
@@ -27,12 +28,19 @@ def lib():
     return _capi.lib()
 
 
-def fetch_schedule(lib, dims, r, T, cutoff):
+def fetch_schedule(lib, dims, r, T, cutoff, reach=None):
     d = (ctypes.c_int64 * len(dims))(*dims)
-    n = lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, None, 0)
+    if reach is None:
+        n = lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, None, 0)
+        assert n > 0
+        buf = (ctypes.c_int64 * n)()
+        assert lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, buf, n) == n
+        return list(buf)
+    rc = (ctypes.c_int * (2 * len(dims)))(*[int(x) for x in np.asarray(reach).ravel()])
+    n = lib.stencil_debug_schedule_reach(len(dims), d, r, rc, T, cutoff, None, 0)
     assert n > 0
     buf = (ctypes.c_int64 * n)()
-    assert lib.stencil_debug_schedule(len(dims), d, r, T, cutoff, buf, n) == n
+    assert lib.stencil_debug_schedule_reach(len(dims), d, r, rc, T, cutoff, buf, n) == n
     return list(buf)
 
 
@@ -45,10 +53,10 @@ def decode(v):
             i += 5
             strips = []
             for _ in range(n):
-                f = v[i:i + 16]
-                i += 16
+                f = v[i:i + 26]
+                i += 26
                 strips.append(dict(bdims=f[0:3], off=f[3:6], valid=f[6:9], perm=f[9:12],
-                                   lo=f[12], hi=f[13], face_axis=f[14], face_side=f[15]))
+                                   lo=f[12:18], hi=f[18:24], face_axis=f[24], face_side=f[25]))
             ops.append(("solve", step, Tk, level, strips))
         elif kind == 2:
             ops.append(("scatter", v[i + 1]))
@@ -57,14 +65,14 @@ def decode(v):
             ops.append(("loop", v[i + 1]))
             i += 2
         elif kind == 3:
-            Tb, n = v[i + 1], v[i + 2]
-            i += 3
+            Tb, wout, n = v[i + 1], v[i + 2:i + 8], v[i + 8]
+            i += 9
             tiles = []
             for _ in range(n):
                 f = v[i:i + 6]
                 i += 6
                 tiles.append((f[0::2], f[1::2]))
-            ops.append(("base", Tb, tiles))
+            ops.append(("base", Tb, tiles, wout))
         else:
             raise AssertionError(f"bad op {kind}")
     return ops
@@ -79,17 +87,28 @@ def region_slices(s, nd):
     return tuple(sl)
 
 
+def _near(delta, bound):
+    """Cells within bound[f] of some face f (delta: face_distances, faces 2a + side)."""
+    m = np.zeros(delta.shape[2:], dtype=bool)
+    for a in range(delta.shape[0]):
+        for s in range(2):
+            m |= delta[a, s] <= bound[2 * a + s]
+    return m
+
+
 def emulate(a0, w, T, ops):
+    """Replay the exported schedule with numpy stand-ins for each kernel. The
+    interior (cells the boundary cannot reach in T steps) comes from the
+    periodic solve of the whole input, as the solver does."""
     dims = a0.shape
     nd = a0.ndim
     r = (w.shape[0] - 1) // 2
-    dist = oracle.boundary_distance(dims)
+    delta = es.face_distances(dims)
     X = a0.copy()
-    maxdist = min(l // 2 for l in dims)
     loop = any(op[0] == "loop" for op in ops)
-    Z = oracle.stencil_fft_periodic(a0, w, T) if r * T < maxdist and not loop else None
+    interior = es.arrival_time(dims, es.face_reach(w)) > T
+    Z = oracle.stencil_fft_periodic(a0, w, T) if interior.any() and not loop else None
     stash = {}
-    grids = np.meshgrid(*[np.arange(l) for l in dims], indexing="ij")
     for op in ops:
         if op[0] == "loop":
             X = oracle.stencil_loop(X, w, op[1], "dirichlet")
@@ -115,16 +134,18 @@ def emulate(a0, w, T, ops):
                 valid = tuple(slice(0, s["valid"][a]) for a in range(nd))
                 back = np.transpose(S[valid], inv)
                 sl_grid = region_slices(s, nd)
-                m = (dist[sl_grid] > s["lo"]) & (dist[sl_grid] <= s["hi"])
+                dl = delta[(slice(None), slice(None)) + sl_grid]
+                m = ~_near(dl, s["lo"])
                 fa = s["face_axis"]
                 if fa >= 0:
-                    g = grids[fa][sl_grid]
-                    df = g + 1 if s["face_side"] == 0 else dims[fa] - g
-                    m &= df <= s["hi"]
+                    f = 2 * fa + s["face_side"]
+                    m &= dl[fa, s["face_side"]] <= s["hi"][f]
+                else:
+                    m &= _near(dl, s["hi"])
                 sub = X[sl_grid]
                 sub[m] = back[m]
         else:
-            _, Tb, tiles = op
+            _, Tb, tiles, wout = op
             h = r * Tb
             Y = X.copy()
             for lo, hi in tiles:
@@ -135,12 +156,12 @@ def emulate(a0, w, T, ops):
                 res = oracle.stencil_loop(sub, w, Tb, "dirichlet")
                 osl = tuple(slice(lo[a], hi[a]) for a in range(nd))
                 rsl = tuple(slice(lo[a] - ilo[a], hi[a] - ilo[a]) for a in range(nd))
-                m = dist[osl] <= r * Tb
+                m = _near(delta[(slice(None), slice(None)) + osl], wout)
                 Y[osl][m] = res[rsl][m]
-            cover = dist <= r * Tb
+            cover = _near(delta, wout)
             X[cover] = Y[cover]
     if Z is not None:
-        X[dist > r * T] = Z[dist > r * T]
+        X[interior] = Z[interior]
     return X
 
 
@@ -261,5 +282,77 @@ def test_automatic_cutoff_keeps_leaf_halos_small(lib, dims, r, T):
     leaves = [o for o in ops if o[0] == "base"]
     assert leaves
     side = (150 * 1024 / 8) ** (1.0 / len(dims))
-    for _, Tb, _tiles in leaves:
+    for _, Tb, _tiles, _wout in leaves:
         assert 4 * r * Tb + 2 * r <= side
+
+
+# ---------------------------------------------------------------------------
+# l-shell regions (appendix "l-shell Spatial Grid Decomposition"): stencils
+# that reach further towards some faces than towards others
+# ---------------------------------------------------------------------------
+def _support(nd, r, offsets, seed):
+    rng = np.random.default_rng(seed)
+    w = np.zeros((2 * r + 1,) * nd)
+    for m in offsets:
+        w[tuple(mm + r for mm in m)] = 0.2 + rng.random()
+    return w / w.sum()
+
+
+SHELL_STENCILS = {
+    "upwind1d": (1, 1, [(-1,), (0,)]),
+    "lean1d": (1, 2, [(-1,), (0,), (2,)]),
+    "upwind2d": (2, 1, [(0, 0), (-1, 0), (0, -1)]),
+    "aniso2d": (2, 2, [(0, 0), (-2, 0), (2, 0), (0, -1), (0, 1), (1, 1)]),
+    "lean2d": (2, 3, [(0, 0), (-1, 0), (3, 0), (0, 2), (0, -1), (1, -1)]),
+    "upwind3d": (3, 1, [(0, 0, 0), (-1, 0, 0), (0, -1, 0), (0, 0, 1), (-1, 0, 1)]),
+}
+
+SHELL_CASES = [("upwind1d", (64,), T, c) for T in (1, 5, 13, 40, 63, 90) for c in (2, 3, 8)] + [
+    ("lean1d", (128,), 31, 4), ("lean1d", (256,), 70, 0), ("lean1d", (64,), 21, 3),
+    ("upwind2d", (64, 64), 40, 4), ("upwind2d", (32, 64), 21, 3), ("upwind2d", (128, 32), 100, 8),
+    ("aniso2d", (64, 32), 9, 2), ("aniso2d", (128, 64), 20, 4), ("lean2d", (64, 64), 9, 3),
+    ("lean2d", (128, 128), 17, 0), ("upwind3d", (16, 16, 32), 9, 2), ("upwind3d", (32, 16, 16), 14, 3),
+]
+
+
+@pytest.mark.parametrize("name,dims,T,cutoff", SHELL_CASES)
+def test_shell_schedule_reproduces_dirichlet_loop(lib, name, dims, T, cutoff):
+    nd, r, offs = SHELL_STENCILS[name]
+    w = _support(nd, r, offs, 300 + T)
+    a0 = wl.grid_uniform(dims, 301 + T)
+    ops = decode(fetch_schedule(lib, dims, r, T, cutoff, es.face_reach(w)))
+    got = emulate(a0, w, T, ops)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(a0)) < 1e-11
+
+
+def test_symmetric_reach_gives_the_distance_schedule(lib):
+    for dims, r, T, c in [((8192, 8192), 1, 4096, 32), ((64, 32), 2, 6, 2), ((16, 16, 16), 1, 5, 2)]:
+        assert fetch_schedule(lib, dims, r, T, c) == fetch_schedule(lib, dims, r, T, c,
+                                                                    [r] * (2 * len(dims)))
+
+
+def test_upwind_schedule_touches_only_the_upwind_faces(lib):
+    # flow towards +x and +y: only the low faces (0 and 2) are ever reached, so
+    # strips and base-case bands sit on those two faces alone
+    ops = decode(fetch_schedule(lib, (4096, 4096), 1, 1024, 16, [1, 0, 1, 0]))
+    strips = [s for o in ops if o[0] == "solve" for s in o[4]]
+    assert strips and all(s["face_axis"] == -1 or s["face_side"] == 0 for s in strips)
+    assert sum(1 for s in strips if s["face_axis"] >= 0) > 0
+    for o in ops:
+        if o[0] == "base":
+            assert o[3][1] == 0 and o[3][3] == 0
+            # every tile lies in a low band: lo of its normal axis is 0
+            assert all(min(lo[0], lo[1]) == 0 for lo, _hi in o[2])
+    # half the strips of the symmetric schedule
+    sym = decode(fetch_schedule(lib, (4096, 4096), 1, 1024, 16))
+    n_sym = sum(len(o[4]) for o in sym if o[0] == "solve")
+    assert len(strips) < 0.6 * n_sym
+
+
+def test_reach_arguments_are_checked(lib):
+    d = (ctypes.c_int64 * 2)(64, 64)
+    bad = [[0, 0, 0, 0], [2, 0, 0, 0], [-1, 1, 1, 1]]
+    for reach in bad:
+        rc = (ctypes.c_int * 4)(*reach)
+        assert lib.stencil_debug_schedule_reach(2, d, 1, rc, 5, 0, None, 0) == -1
