@@ -434,7 +434,8 @@ def generalization_lines(flush, check, workers, world):
     events (L2 flushed between steps) and checked against the oracle:
     mixed-radix 8000^2 (the paper's seidel2d size, T = 1e5), implicit
     Crank-Nicolson 4096^2, two coupled fields 2048^2, reflecting boundary
-    2048^2, and the mixed-shape batch executor."""
+    2048^2, an upwind stencil on l-shell regions at 8192^2, and the
+    mixed-shape batch executor."""
     import numpy as np
     import torch
     from paper_2105_06676_gb300 import BatchExecutor, StencilPlan, VectorStencilPlan
@@ -523,6 +524,31 @@ def generalization_lines(flush, check, workers, world):
         "workload": "box9_2d_reflecting_2048x2048_T1000_fp32", "ms_per_step": ms,
         "value": world * dims[0] * dims[1] * T / (ms * 1e-3), "err_vs_oracle": err,
         "tolerance": 2e-4, "oracle": "FP64 periodic solve of the even extension"}
+    del a0, res
+
+    # l-shell regions: first-order upwind stencil (reaches only the two low
+    # faces), zero Dirichlet, 8192^2, T = 4096 -- the box9 Dirichlet line's size
+    wup = np.zeros((3, 3))
+    wup[1, 1], wup[0, 1], wup[1, 0] = 0.5, 0.3, 0.2      # a_t[i] , a_t[i - e0], a_t[i - e1]
+    dims, T = (8192, 8192), 4096
+    a0 = wl.grid_uniform(dims, 7006)
+    plan = StencilPlan(dims, wup, "dirichlet", "fp32")
+    plan.run(torch.tensor(a0, dtype=torch.float32, device="cuda"), T)   # schedule set-up
+    ms, res = timed(plan, a0, T, steps=3)
+    plan.close()
+    errs = []
+    if check:
+        # a cell's T-step cone spans [i - T, i] x [j - T, j]: the loop on that
+        # box (Dirichlet zeros below row / column 0) gives it exactly
+        for (i, j) in [(0, 0), (0, 8191), (7, 4000), (40, 40), (40, 8191), (8191, 10), (300, 9)]:
+            i0, j0 = max(0, i - T), max(0, j - T)
+            box = oracle.stencil_loop(a0[i0:i + 1, j0:j + 1], wup, T, "dirichlet")
+            errs.append(abs(float(res[i, j]) - box[i - i0, j - j0]) / np.max(np.abs(a0)))
+    out["upwind_shells_8192sq"] = {
+        "workload": "upwind3_2d_dirichlet_8192x8192_T4096_fp32 (l-shell regions: two faces)",
+        "ms_per_step": ms, "value": world * dims[0] * dims[1] * T / (ms * 1e-3),
+        "err_vs_oracle_max": max(errs) if errs else None, "err_vs_oracle_sampled": len(errs),
+        "tolerance": 2e-4, "oracle": "FP64 loop over each sampled cell's dependence cone"}
     del a0, res
 
     # batch executor: 512 mixed small periodic requests in one persistent launch
