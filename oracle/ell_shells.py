@@ -157,3 +157,32 @@ def stencil_fft_aperiodic_shells(a0: np.ndarray, weights: np.ndarray, T: int, cu
         near = recursive_boundary_shells(a0, weights, T, cutoff, boundary, reach)
         result[~interior] = near[~interior]
     return result
+
+
+def upwind_dirichlet_closed_form(a0: np.ndarray, p, T: int, cells) -> np.ndarray:
+    """a_T at the given cells for the 2-D stencil p0 a[i] + p1 a[i - e0] +
+    p2 a[i - e1] on a zero-Dirichlet grid (closed form, no recursion).
+
+    The stencil looks only towards the two low faces, so the grid evolves as
+    the free-space problem with a0 extended by zeros below index 0 (those
+    cells read only cells further below, all zero, and stay zero; the high
+    faces are never read). The T-fold convolution power of the stencil is
+    the trinomial distribution K_T(dx, dy) = T! / (k! dx! dy!) p0^k p1^dx
+    p2^dy with k = T - dx - dy, so
+        a_T(i, j) = sum over 0 <= dx <= i, 0 <= dy <= j of K_T(dx, dy) a0(i - dx, j - dy),
+    evaluated in FP64 through log-gamma."""
+    from scipy.special import gammaln
+    a0 = np.asarray(a0, dtype=np.float64)
+    dx = np.arange(T + 1)[:, None]
+    dy = np.arange(T + 1)[None, :]
+    k = T - dx - dy
+    kc = np.maximum(k, 0)
+    logK = (gammaln(T + 1) - gammaln(kc + 1) - gammaln(dx + 1) - gammaln(dy + 1)
+            + kc * np.log(p[0]) + dx * np.log(p[1]) + dy * np.log(p[2]))
+    K = np.where(k >= 0, np.exp(logK), 0.0)
+    out = []
+    for i, j in cells:
+        mi, mj = min(i, T), min(j, T)
+        win = a0[i - mi:i + 1, j - mj:j + 1][::-1, ::-1]
+        out.append(float(np.sum(K[:mi + 1, :mj + 1] * win)))
+    return np.array(out)

@@ -2002,6 +2002,10 @@ void aperiodic_forget_schedules(stencil_plan_s* p) {
             p->ap->bytes -= periodic_workspace_bytes(p->ndim, v.bdims, p->precision);
         }
     p->ap->schedules.clear();
+    // base-case tiles and measured choices depend on the reach towards every face
+    for (auto& kv : p->ap->base) cudaFree(kv.second.tiles);
+    p->ap->base.clear();
+    p->ap->tuned.clear();
 }
 
 size_t aperiodic_bytes(const stencil_plan_s* p) { return p && p->ap ? p->ap->bytes : 0; }

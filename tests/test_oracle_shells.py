@@ -162,3 +162,16 @@ def test_ranges_without_the_away_reach_are_wrong():
     assert np.max(np.abs(lit[near] - ref[near])) > 1e-3
     good = es.recursive_boundary_shells(a0, w, T, 4)
     assert np.max(np.abs(good[near] - ref[near])) < 1e-12
+
+
+@pytest.mark.parametrize("dims,T", [((128, 96), 57), ((64, 200), 150), ((40, 40), 100)])
+def test_upwind_closed_form_matches_loop(dims, T):
+    w = np.zeros((3, 3))
+    w[1, 1], w[0, 1], w[1, 0] = 0.5, 0.3, 0.2
+    a0 = wl.grid_uniform(dims, 70 + T)
+    ref = oracle.stencil_loop(a0, w, T, "dirichlet")
+    rng = np.random.default_rng(T)
+    cells = [(0, 0), (dims[0] - 1, dims[1] - 1)] + [
+        (int(rng.integers(dims[0])), int(rng.integers(dims[1]))) for _ in range(20)]
+    got = es.upwind_dirichlet_closed_form(a0, (0.5, 0.3, 0.2), T, cells)
+    np.testing.assert_allclose(got, [ref[c] for c in cells], rtol=0, atol=1e-13)
