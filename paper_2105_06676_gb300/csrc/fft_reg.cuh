@@ -68,11 +68,13 @@ template <int DIR, typename C>
 __device__ __forceinline__ void reg_twiddle(C* v, int k, int sh, const C* __restrict__ tw) {
     if (k == 0) return;
     if constexpr (sizeof(C) == 8) {
-        // FP32: four table loads, the rest by products (<= 3 roundings deep)
+        // FP32: two table loads (w^k, w^4k), the rest by products (<= 3
+        // roundings deep); the loads of w^8k and w^12k would touch a sector per
+        // lane for the strided k of the last stages
         const C w1 = twiddle(tw, k << sh, DIR);
         const C w4 = twiddle(tw, (4 * k) << sh, DIR);
-        const C w8 = twiddle(tw, (8 * k) << sh, DIR);
-        const C w12 = twiddle(tw, (12 * k) << sh, DIR);
+        const C w8 = cmul(w4, w4);
+        const C w12 = cmul(w8, w4);
         const C w2 = cmul(w1, w1);
         const C w3 = cmul(w2, w1);
         const C base[4] = {C{1, 0}, w4, w8, w12};

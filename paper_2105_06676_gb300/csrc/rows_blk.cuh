@@ -46,15 +46,25 @@ __host__ __device__ constexpr int blk_nx(int log2n, int cl) {
 }
 __host__ __device__ constexpr size_t blk_smem(int log2n, int cl) {
     const size_t ex = (size_t)blk_rows(log2n) * blk_seq_stride(log2n);
-    const size_t st = (size_t)blk_nx(log2n, cl) * blk_rows(log2n) * (1 << cl);
+    // staging, rounded up to whole 128-byte rows (the swizzle permutes within them)
+    const size_t st = ((size_t)blk_nx(log2n, cl) * blk_rows(log2n) * (1 << cl) + 15) / 16 * 16;
     return (ex > st ? ex : st) * 8;
 }
 
-// Staging position of X[c][k] (row c of the CTA): block-major, rows within a
-// block, columns within a row: the order of the global runs.
+// The staging area holds 16-byte pieces (two complex values) in the order of
+// the global runs; piece p lives at slot p ^ (3 (p / 8) mod 8), a permutation
+// within each 128-byte row. A warp's element accesses (one row of the CTA,
+// 32 consecutive columns: every RPT-th run of CPT values) then spread over all
+// banks instead of hitting the same RPT-th of them, while a warp's 16-byte
+// piece accesses (32 consecutive pieces, four whole rows) stay conflict-free.
+__device__ __forceinline__ int blk_piece(int p) { return p ^ ((3 * (p >> 3)) & 7); }
+
+// Staging position (in complex values) of X[c][k], row c of the CTA: block-major,
+// rows within a block, columns within a row, pieces swizzled as above.
 template <int CL, int RPT>
 __device__ __forceinline__ int blk_stage(int c, int k) {
-    return ((k >> CL) * RPT + c) * (1 << CL) + (k & ((1 << CL) - 1));
+    const int s = ((k >> CL) * RPT + c) * (1 << CL) + (k & ((1 << CL) - 1));
+    return (blk_piece(s >> 1) << 1) | (s & 1);
 }
 
 // R2C: rows of the real grid (viewed as n complex pairs) -> blocked half spectra.
@@ -80,8 +90,11 @@ k_rows_r2c_blk(const float2* __restrict__ grid, float2* __restrict__ H, int l0_l
 #pragma unroll
     for (int r = 0; r < 16; ++r) sv[j + q * r] = v[r];
     __syncthreads();
-    // real-input split: X[k] from Z[k] and Z[n-k]
-    const int sh = twn_log2 - LOG2N - 1;   // W^k = exp(-2 pi i k / 2n) = tw[k << sh]
+    // real-input split: X[k] from Z[k] and Z[n-k]. W^k = exp(-2 pi i k / 2n)
+    // = tw[k << sh] is taken as W^j W^(q r): one per-thread load and sixteen
+    // loads that are the same for the whole warp
+    const int sh = twn_log2 - LOG2N - 1;
+    const float2 wj = __ldg(tw + (j << sh));
     float2 xn{0.f, 0.f};
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -89,7 +102,8 @@ k_rows_r2c_blk(const float2* __restrict__ grid, float2* __restrict__ H, int l0_l
         const float2 zk = v[r], znk = sv[(n - k) & (n - 1)];
         const float2 xe = cscale(cadd(zk, cconj(znk)), 0.5f);
         const float2 xo = cscale(cmul_mi(csub(zk, cconj(znk))), 0.5f);
-        v[r] = cadd(xe, cmul(__ldg(tw + (k << sh)), xo));
+        const float2 wk = r == 0 ? wj : cmul(wj, __ldg(tw + ((q * r) << sh)));
+        v[r] = cadd(xe, cmul(wk, xo));
         if (k == 0) xn = csub(xe, xo);   // X[n] = Xe[0] - Xo[0]
     }
     __syncthreads();   // every partner read is done: the buffer becomes the staging area
@@ -117,7 +131,7 @@ k_rows_r2c_blk(const float2* __restrict__ grid, float2* __restrict__ H, int l0_l
         if (p < PIECES) {
             const int x = p / (RPT * PPR);
             const int rem = p - x * (RPT * PPR);
-            if (rem / PPR < rows_live) hz[(long long)x * (l0 * PPR) + rem] = st[p];
+            if (rem / PPR < rows_live) hz[(long long)x * (l0 * PPR) + rem] = st[blk_piece(p)];
         }
     }
 }
@@ -161,18 +175,19 @@ k_rows_c2r_blk(const float2* __restrict__ H, float2* __restrict__ grid, int l0_l
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int p = threadIdx.x + u * blk_threads(LOG2N);
-            if (p < PIECES) st[p] = t[u];
+            if (p < PIECES) st[blk_piece(p)] = t[u];
         }
     }
     __syncthreads();
     const int sh = twn_log2 - LOG2N - 1;
+    const float2 wj = __ldg(tw + (j << sh));   // W^k = W^j W^(q s), as in the R2C split
     float2 v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
         const int k = j + q * s;
         const float2 yk = buf[blk_stage<CL, RPT>(c, k)];
         const float2 ynk = buf[blk_stage<CL, RPT>(c, n - k)];
-        const float2 wk = __ldg(tw + (k << sh));
+        const float2 wk = s == 0 ? wj : cmul(wj, __ldg(tw + ((q * s) << sh)));
         v[s] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
     }
     __syncthreads();   // staging read: the buffer becomes the exchange buffer
