@@ -37,9 +37,13 @@ __host__ __device__ constexpr int blk_threads(int log2n) {
 __host__ __device__ constexpr int blk_rows(int log2n) {
     return blk_threads(log2n) / ((1 << log2n) >> 4);
 }
-// Sequence stride of the exchange buffer (seq_stride of fft_common.cuh).
+// Sequence stride of the exchange buffer: the FFT's exchanges use one pad
+// slot per 16 elements (PadLayout<0, 4>), which keeps every exchange of every
+// stage free of bank conflicts for 8-byte elements, half a warp per wavefront
+// (one pad per 32 left the stride-R0 stores of the first exchange and the
+// Ns = 8 stores of a 2048-point transform two-way conflicted).
 __host__ __device__ constexpr int blk_seq_stride(int log2n) {
-    return (1 << log2n) + ((1 << log2n) >> 5) + 1;
+    return (1 << log2n) + ((1 << log2n) >> 4) + 1;
 }
 __host__ __device__ constexpr int blk_nx(int log2n, int cl) {
     return ((1 << log2n) + 1 + (1 << cl) - 1) >> cl;
@@ -86,7 +90,7 @@ k_rows_r2c_blk(const float2* __restrict__ grid, float2* __restrict__ H, int l0_l
     float2 v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = live ? __ldg(rowp + j + q * s) : float2{0.f, 0.f};
-    ct_fft<-1, LOG2N, 0, 5>(v, buf + c * SS, j, tw, twn_log2);
+    ct_fft<-1, LOG2N, 0, 4>(v, buf + c * SS, j, tw, twn_log2);
 #pragma unroll
     for (int r = 0; r < 16; ++r) sv[j + q * r] = v[r];
     __syncthreads();
@@ -191,7 +195,7 @@ k_rows_c2r_blk(const float2* __restrict__ H, float2* __restrict__ grid, int l0_l
         v[s] = cadd(cadd(yk, cconj(ynk)), cmul_i(cmul(cconj(wk), csub(yk, cconj(ynk)))));
     }
     __syncthreads();   // staging read: the buffer becomes the exchange buffer
-    ct_fft<+1, LOG2N, 0, 5>(v, buf + c * SS, j, tw, twn_log2);
+    ct_fft<+1, LOG2N, 0, 4>(v, buf + c * SS, j, tw, twn_log2);
     bool bad = false;
     if (live) {
         float2* out = grid + row * n;
