@@ -68,6 +68,12 @@ typedef struct stencil_plan_s* stencil_plan_t;
  * the radius must not exceed any axis length. Both aperiodic conditions use
  * RecursiveBoundary (paper Sec. 5): its periodic solves keep only cells the
  * boundary cannot reach, and the condition enters through the base-case loop.
+ * The regions are cut per face from the weights (appendix "l-shell Spatial
+ * Grid Decomposition"): the largest offset towards a face among the nonzero
+ * weights sets how far the boundary reaches through it per step, so a biased
+ * or upwind stencil gets narrower regions and a face that no offset looks
+ * towards gets none; zero weights at the edge of the (2r+1)^ndim box cost
+ * nothing. A symmetric box stencil gets the distance bands of Sec. 5.2.
  */
 enum stencil_boundary { STENCIL_PERIODIC = 0, STENCIL_ZERO_DIRICHLET = 1, STENCIL_NEUMANN = 2 };
 enum stencil_precision {
