@@ -357,6 +357,17 @@ int64_t stencil_debug_schedule_reach(int ndim, const int64_t* dims, int radius, 
                                      int64_t T, int64_t cutoff, int64_t* out, int64_t cap);
 
 /*
+ * Host-only: the toward-reach a plan derives from its weights, the input of
+ * the l-shell regions above. weights: (2 radius + 1)^ndim doubles laid out as
+ * for stencil_plan; writes reach[2 a + side] for a < ndim (side 0: the face
+ * below index 0, the largest -m_a over the nonzero weights; side 1: the face
+ * above the last index, the largest +m_a; 0 where no offset points that way).
+ * Returns STENCIL_OK or STENCIL_EINVAL (null pointer, ndim outside 1..3,
+ * radius outside 0..3).
+ */
+int stencil_debug_face_reach(int ndim, int radius, const double* weights, int* reach);
+
+/*
  * Periodic solve that allocates nothing. The paper has no counterpart: this
  * entry point serves callers that cannot allocate device memory when they
  * solve (a latency-critical loop that cannot pay cudaMalloc's implicit device

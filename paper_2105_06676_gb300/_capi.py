@@ -62,6 +62,7 @@ SIGNATURES = [
                                             _i64p, _c.c_int64]),
     ("stencil_debug_schedule_reach", _c.c_int64, [_c.c_int, _i64p, _c.c_int, _c.POINTER(_c.c_int),
                                                   _c.c_int64, _c.c_int64, _i64p, _c.c_int64]),
+    ("stencil_debug_face_reach", _c.c_int, [_c.c_int, _c.c_int, _dp, _c.POINTER(_c.c_int)]),
 ]
 
 class StencilRequest(ctypes.Structure):

@@ -993,6 +993,18 @@ extern "C" int stencil_plan_set_weights(stencil_plan_t p, int radius, const doub
     return STENCIL_OK;
 }
 
+extern "C" int stencil_debug_face_reach(int ndim, int radius, const double* weights, int* reach) {
+    if (!weights || !reach || ndim < 1 || ndim > 3 || radius < 0 || radius > kMaxRadius)
+        return STENCIL_EINVAL;
+    int r[3][2];
+    face_reach(weights, ndim, radius, r);
+    for (int a = 0; a < ndim; ++a) {
+        reach[2 * a] = r[a][0];
+        reach[2 * a + 1] = r[a][1];
+    }
+    return STENCIL_OK;
+}
+
 extern "C" int stencil_plan_set_cutoff(stencil_plan_t p, int64_t cutoff) {
     if (!p || (cutoff != 0 && cutoff < 2)) return STENCIL_EINVAL;
     if (p->cutoff != cutoff) aperiodic_forget_schedules(p);

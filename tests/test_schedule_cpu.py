@@ -356,3 +356,46 @@ def test_reach_arguments_are_checked(lib):
     for reach in bad:
         rc = (ctypes.c_int * 4)(*reach)
         assert lib.stencil_debug_schedule_reach(2, d, 1, rc, 5, 0, None, 0) == -1
+
+
+def _plan_reach(lib, w):
+    nd = w.ndim
+    r = (w.shape[0] - 1) // 2
+    out = (ctypes.c_int * (2 * nd))()
+    wc = np.ascontiguousarray(w, dtype=np.float64)
+    assert lib.stencil_debug_face_reach(nd, r, wc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out) == 0
+    return np.array(list(out)).reshape(nd, 2)
+
+
+def test_plan_face_reach_matches_the_oracle(lib):
+    # the reach a plan derives from its weights (the l-shell regions' input)
+    # against the oracle's, on random sparse supports of every dimension and radius
+    rng = np.random.default_rng(400)
+    for nd in (1, 2, 3):
+        for r in (0, 1, 2, 3):
+            for _ in range(25):
+                w = rng.random((2 * r + 1,) * nd) * (rng.random((2 * r + 1,) * nd) < 0.3)
+                np.testing.assert_array_equal(_plan_reach(lib, w), es.face_reach(w))
+    for name, (nd, r, offs) in SHELL_STENCILS.items():
+        w = _support(nd, r, offs, 401)
+        np.testing.assert_array_equal(_plan_reach(lib, w), es.face_reach(w))
+
+
+def test_plan_reach_drives_the_schedule_end_to_end(lib):
+    # weights -> the library's reach -> the library's schedule -> replay == loop
+    nd, r, offs = SHELL_STENCILS["lean2d"]
+    w = _support(nd, r, offs, 402)
+    a0 = wl.grid_uniform((64, 128), 403)
+    T = 13
+    ops = decode(fetch_schedule(lib, (64, 128), r, T, 3, _plan_reach(lib, w)))
+    got = emulate(a0, w, T, ops)
+    assert np.max(np.abs(got - oracle.stencil_loop(a0, w, T, "dirichlet"))) / np.max(np.abs(a0)) < 1e-11
+
+
+def test_face_reach_rejects_bad_arguments(lib):
+    w = np.ones(3)
+    out = (ctypes.c_int * 2)()
+    dp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.stencil_debug_face_reach(0, 1, dp, out) == -1
+    assert lib.stencil_debug_face_reach(1, 4, dp, out) == -1
+    assert lib.stencil_debug_face_reach(1, 1, None, out) == -1
